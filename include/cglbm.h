@@ -1,0 +1,179 @@
+/*
+ * cglbm.h -- C ABI of the B300 colour-gradient lattice Boltzmann library.
+ *
+ * One context holds one lattice: two immiscible fluid components (liquid
+ * reactant r, gas product p) on D3Q19 and a dissolved reactant C on D3Q7,
+ * inside a static porous solid.  One call of lbm_step advances the lattice by
+ * whole time steps of the method of Beunen & Harting, "Gas-generating reactive
+ * flows in bicontinuous catalyst support structures":
+ *
+ *   pull streaming with halfway bounce-back        Sec. 2.2, Eq. bounce_back
+ *   colour field, extrapolated into the solid      Eq. color_function,
+ *                                                   Eq. color_lattice_weighted_average
+ *   isotropic gradient, normal, wetting            Eq. finite_difference_scheme,
+ *                                                   Eq. color_gradient_normal,
+ *                                                   Eq. realigned_normal_vectors,
+ *                                                   Eq. normal_vector_solid
+ *   curvature, CSF force, exact-difference shift   Eq. interface_curvature,
+ *                                                   Eq. continuum_surface_force,
+ *                                                   Eq. operator_perturbation
+ *   central-moment collision                       Appendix A, Eq. collision_operator,
+ *                                                   Eq. back_transformation_vector
+ *   recolouring                                    Eq. operator_recoloring
+ *   surface reaction                               Eq. reactive_boundary_condition_*
+ * and reports the observables of Sec. 5.1 (Eq. reactant_mass,
+ * Eq. product_mass, Eq. production_rate).  The advection-diffusion lattice for
+ * C and the inlet/outlet column boundaries are additions of this library (the
+ * paper converts rho^r into rho^p directly and uses periodic boxes only);
+ * reaction_mode = 1 selects the paper's direct conversion.
+ *
+ * Conventions
+ *   - Lattice index of node (x, y, z): (z * ny + y) * nx + x, x fastest.
+ *   - Populations: 45 per node, population-major ("structure of arrays"):
+ *     f^r_0..18, f^p_0..18, g_0..6.  D3Q19 order is the column order of the
+ *     paper's matrix M (Sec. 2.1), rest vector last; D3Q7 order is
+ *     +x, -x, +y, -y, +z, -z, rest.  A state buffer for lbm_get_state /
+ *     lbm_set_state holds 45 * nx * ny * nz floats, index p * N + node.
+ *   - All host pointers are read or written synchronously inside the call and
+ *     are not retained; the caller keeps ownership.  The library owns every
+ *     device allocation of a context.  The CUDA stream passed in lbm_params is
+ *     borrowed and must outlive the context.
+ *   - Every function returns LBM_OK (0) or a negative code; none aborts.
+ *     Kernel faults are asynchronous: lbm_step returns launch errors, and the
+ *     next synchronising call (lbm_observables, lbm_get_*) returns the
+ *     execution error.  A context that returned LBM_ECUDA should be destroyed.
+ */
+#ifndef CGLBM_H
+#define CGLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)   /* bad dimensions, parameters, sizes or null pointers     */
+#define LBM_ENOMEM (-2)   /* device allocation failed                               */
+#define LBM_ECUDA (-3)    /* CUDA launch or execution error                         */
+#define LBM_ENAN (-4)     /* observables found a non-finite or non-positive density */
+
+typedef struct lbm_ctx lbm_ctx;   /* opaque, library-owned */
+
+typedef struct {
+  int32_t nx, ny, nz;        /* lattice size, each >= 1; nz >= 2 in column mode   */
+  const uint8_t *solid;      /* host, nx*ny*nz bytes, nonzero = solid node s(x)=1   */
+  const uint8_t *reactive;   /* host, optional r(x) (Sec. 2.2); NULL = every fluid
+                                node with at least one solid nearest neighbour     */
+  int32_t bc_z;              /* 0: periodic in z (paper, Sec. 2.2);
+                                1: velocity inlet at z=0, pressure outlet at z=nz-1
+                                (added by this library); x and y always periodic  */
+} lbm_geometry;
+
+typedef struct {
+  double tau;         /* relaxation time, > 0.5; nu = (tau - 1/2)/3 (Eq. kinematic_viscosity) */
+  double sigma;       /* surface tension (Eq. continuum_surface_force)                        */
+  double beta;        /* recolouring parameter (Eq. operator_recoloring)                      */
+  double theta_deg;   /* contact angle in degrees, measured through the r phase               */
+  double accel[3];    /* body acceleration a^k, same for both components                      */
+  double diffusivity; /* D of the reactant C (D3Q7 BGK, tau_g = 4 D + 1/2), > 0               */
+  double k_rate;      /* first-order surface rate k of the C-mode reaction                    */
+  double c_init;      /* initial C for lbm_create's default start                             */
+  double c_in;        /* inlet C (column mode)                                                */
+  double u_in;        /* inlet velocity along +z (column mode)                                */
+  double rho_out;     /* outlet density (column mode)                                         */
+  double xi;          /* reaction rate of the paper's mode (Eq. reactive_boundary_condition_*) */
+  int32_t reaction_mode; /* 0: delta = min(k NN r C psi, C, rho^r), C on D3Q7;
+                            1: delta = min(xi NN r, 1) rho^r, C not evolved                  */
+  int32_t storage;    /* population storage: 0 = FP32 (only value accepted)                  */
+  void *cuda_stream;  /* cudaStream_t to launch on (borrowed); NULL = legacy default stream  */
+} lbm_params;
+
+typedef struct {
+  double mass_r;          /* sum over fluid nodes of rho^r (Eq. reactant_mass)               */
+  double mass_p;          /* sum of rho^p (Eq. product_mass)                                 */
+  double mass_c;          /* sum of the reactant C                                           */
+  double consumed;        /* cumulative sum of the reaction amounts delta since the start    */
+  double rate;            /* sum of delta in the last step, = -dm^r/dt (Eq. production_rate) */
+  double conversion;      /* periodic: consumed / m^C(0); column: 1 - flux_out / flux_in     */
+  double gas_saturation;  /* mean over fluid nodes of (1 - rho^N)/2                          */
+  double flux_in;         /* sum over fluid nodes of plane z=0 of u_z C                      */
+  double flux_out;        /* same over plane z=nz-1                                          */
+  int64_t step;           /* time steps taken since the state was last set                   */
+  int64_t n_fluid;        /* number of fluid nodes                                           */
+  int64_t n_bad;          /* fluid nodes with non-finite or non-positive rho^r + rho^p       */
+} lbm_obs;
+
+/* Intermediate fields of the last completed step (lbm_get_field), one float
+ * per node unless noted.  Values at solid nodes are 0 except where noted. */
+#define LBM_FIELD_RHON 0     /* rho^N, with the Eq. color_lattice_weighted_average values
+                                at solid nodes next to the fluid                           */
+#define LBM_FIELD_NORMAL 1   /* 3 floats per node (n_x, n_y, n_z), plane-major [3][N]:
+                                wetted n at fluid nodes, averaged n at boundary solids      */
+#define LBM_FIELD_GRADMAG 2  /* |grad rho^N| at fluid nodes                                */
+#define LBM_FIELD_NS 3       /* 3 floats per node, [3][N]: solid normal n_s at wall nodes  */
+#define LBM_FIELD_NN 4       /* NN(x) (Eq. nearest_solid_neighbors)                        */
+#define LBM_FIELD_CURV 5     /* H (Eq. interface_curvature); needs lbm_set_debug(ctx, 1)   */
+#define LBM_FIELD_DELTA 6    /* reaction amount delta of the last step; needs debug        */
+
+/* Create a context: validates, copies the geometry to the device, builds the
+ * static per-node data (bounce-back links, NN, r, wall flags, solid normals)
+ * on the GPU, and sets the equilibrium start rho^r = 1, rho^p = 0, u = 0,
+ * C = c_init.  *out is set only on success. */
+int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the context's stream. */
+int lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Reduce the observables of the current (post-collision) state in FP64 on the
+ * device, synchronise the stream and copy them to *out.  Returns LBM_ENAN
+ * (with *out filled) if a fluid node holds a non-finite or non-positive density. */
+int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
+
+/* Synchronise and copy the reaction sums kept by the step kernel (no extra
+ * kernel): *rate = sum of delta in the last step, *consumed = cumulative sum.
+ * Either pointer may be NULL.  This is the cheap per-step result read. */
+int lbm_reaction(lbm_ctx *ctx, double *rate, double *consumed);
+
+/* Equilibrium start from host fields of N floats each (u: 3*N, [3][N], or
+ * NULL for rest): f^r = f^eq(rho_r, u), f^p = f^eq(rho_p, u), g = g^eq(conc, u).
+ * Resets step, consumed and m^C(0). */
+int lbm_init_fields(lbm_ctx *ctx, const float *rho_r, const float *rho_p,
+                    const float *conc, const float *u);
+
+/* Copy the current populations (45 * N floats, layout above) to / from host.
+ * bytes must equal 45 * N * sizeof(float).  lbm_set_state resets step,
+ * consumed and m^C(0), and rebuilds the column ghost planes from the state. */
+int lbm_get_state(lbm_ctx *ctx, float *host_dst, size_t bytes);
+int lbm_set_state(lbm_ctx *ctx, const float *host_src, size_t bytes);
+
+/* Copy one LBM_FIELD_* of the last step to host; bytes must match exactly. */
+int lbm_get_field(lbm_ctx *ctx, int32_t which, float *host_dst, size_t bytes);
+
+/* 1: the step also stores H and delta per node (extra traffic; for checks). */
+int lbm_set_debug(lbm_ctx *ctx, int32_t enable);
+
+/* Per-kernel timing with CUDA events on the context's stream.  Kernel kinds:
+ * 0 density, 1 solid colour, 2 normal, 3 solid normal, 4 main step,
+ * 5 observables.  lbm_profile(ctx, 1) resets and starts; lbm_profile_read
+ * synchronises and returns total milliseconds and launch counts (n <= 6). */
+#define LBM_NKERNELS 6
+int lbm_profile(lbm_ctx *ctx, int32_t enable);
+int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches, int32_t n);
+
+/* Static counts: fluid nodes, wall nodes, solid nodes next to the fluid,
+ * device bytes held.  Any pointer may be NULL. */
+int lbm_info(lbm_ctx *ctx, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd,
+             int64_t *device_bytes);
+
+/* Release every device resource of the context; NULL is ignored. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Static description of an error code. */
+const char *lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGLBM_H */

@@ -31,7 +31,7 @@ from .lattice import (
 
 class PointwiseStep:
     def __init__(self, F, solid, params, reactive=None):
-        self.F = np.asarray(F, dtype=np.float64)
+        self.F = np.asarray(F)   # any float dtype; every access converts to a Python float (FP64)
         self.solid = np.asarray(solid, dtype=bool)
         self.p = params
         self.nz, self.ny, self.nx = self.solid.shape
@@ -97,8 +97,8 @@ class PointwiseStep:
             if p < 19:
                 return W19L[p] * self.p.rho_out
             return 0.0
-        fr = [self.F[i, z, y, x] for i in range(19)]
-        fp = [self.F[19 + i, z, y, x] for i in range(19)]
+        fr = [float(self.F[i, z, y, x]) for i in range(19)]
+        fp = [float(self.F[19 + i, z, y, x]) for i in range(19)]
         if p >= 38:
             return float(self.F[p, z, y, x])
         fm = [a + b for a, b in zip(fr, fp)]

@@ -1,0 +1,535 @@
+// Host side of the C ABI declared in include/cglbm.h: context, device memory,
+// launch sequence of one time step, observables, state transfer, profiling.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cglbm.h"
+#include "kernels.cuh"
+
+using namespace cglbm;
+
+struct lbm_ctx {
+  int device = 0;
+  Lattice L{};
+  lbm_params prm{};
+  StepParams sp{};
+  cudaStream_t stream = nullptr;
+  // device memory (library-owned)
+  float *fa = nullptr, *fb = nullptr;   // current / next populations (with ghost planes)
+  uint32_t *link = nullptr;
+  float4 *ns = nullptr;
+  float *rhoN = nullptr;
+  float4 *nrm = nullptr;
+  uint32_t *bnd_list = nullptr;         // solid nodes next to the fluid
+  long long n_bnd = 0;
+  double *acc = nullptr;                // [0] cumulative delta, [2 + s] per-step delta slots
+  double *obs = nullptr;                // 8 observables accumulators
+  float *dbg_H = nullptr, *dbg_delta = nullptr;
+  bool debug = false;
+  size_t device_bytes = 0;
+  // host-side bookkeeping
+  int64_t step = 0;
+  double mc0 = 0.0;
+  long long n_fluid = 0, n_wall = 0;
+  bool have_fields = false;             // rhoN / nrm hold the last step's values
+  int sticky = LBM_OK;
+  // profiling
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  bool profiling = false;
+};
+
+namespace {
+
+int cuda_fail(lbm_ctx *c, cudaError_t e) {
+  if (e == cudaSuccess) return LBM_OK;
+  if (c) c->sticky = LBM_ECUDA;
+  return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_); \
+  } while (0)
+
+int dalloc(lbm_ctx *c, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  c->device_bytes += bytes;
+  return LBM_OK;
+}
+
+dim3 node_block() { return dim3(32, 4, 1); }
+dim3 node_grid(const Lattice &L) { return dim3((L.nx + 31) / 32, (L.ny + 3) / 4, L.nz); }
+
+void prof_begin(lbm_ctx *c, int kind) {
+  if (!c->profiling || c->ev_used + 2 > c->ev.size()) return;
+  cudaEventRecord(c->ev[c->ev_used], c->stream);
+  c->ev_kind[c->ev_used / 2] = kind;
+}
+void prof_end(lbm_ctx *c) {
+  if (!c->profiling || c->ev_used + 2 > c->ev.size()) return;
+  cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+  c->ev_used += 2;
+}
+
+void free_all(lbm_ctx *c) {
+  cudaFree(c->fa);
+  cudaFree(c->fb);
+  cudaFree(c->link);
+  cudaFree(c->ns);
+  cudaFree(c->rhoN);
+  cudaFree(c->nrm);
+  cudaFree(c->bnd_list);
+  cudaFree(c->acc);
+  cudaFree(c->obs);
+  cudaFree(c->dbg_H);
+  cudaFree(c->dbg_delta);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+}
+
+int check_params(const lbm_params *p) {
+  if (!p) return LBM_EINVAL;
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LBM_EINVAL;
+  if (!(p->diffusivity > 0.0) || !std::isfinite(p->diffusivity)) return LBM_EINVAL;
+  if (!(p->beta >= 0.0) || !std::isfinite(p->sigma) || !std::isfinite(p->theta_deg)) return LBM_EINVAL;
+  if (p->reaction_mode != 0 && p->reaction_mode != 1) return LBM_EINVAL;
+  if (p->storage != 0) return LBM_EINVAL;
+  if (!(p->k_rate >= 0.0) || !(p->xi >= 0.0) || !(p->rho_out > 0.0)) return LBM_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->accel[a])) return LBM_EINVAL;
+  return LBM_OK;
+}
+
+void fill_step_params(lbm_ctx *c) {
+  const lbm_params &p = c->prm;
+  StepParams &s = c->sp;
+  s.omega_cm = (float)(1.0 - 1.0 / p.tau);
+  s.half_sigma = (float)(0.5 * p.sigma);
+  s.beta = (float)p.beta;
+  const double th = p.theta_deg * 3.14159265358979323846 / 180.0;
+  s.cos_th = (float)std::cos(th);
+  s.sin_th = (float)std::sin(th);
+  s.ax = (float)p.accel[0];
+  s.ay = (float)p.accel[1];
+  s.az = (float)p.accel[2];
+  s.inv_tau_g = (float)(1.0 / (4.0 * p.diffusivity + 0.5));
+  s.k_rate = (float)p.k_rate;
+  s.xi = (float)p.xi;
+  s.rho_out = (float)p.rho_out;
+  s.reaction_mode = p.reaction_mode;
+}
+
+// reduce observables of the current state into c->obs (async)
+int launch_observables(lbm_ctx *c) {
+  CK(cudaMemsetAsync(c->obs, 0, 8 * sizeof(double), c->stream));
+  prof_begin(c, 5);
+  k_observables<<<node_grid(c->L), node_block(), 0, c->stream>>>(c->L, c->fa, c->link, c->obs);
+  prof_end(c);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+// after the state changed: ghost planes, counters, m^C(0)
+int reset_after_state(lbm_ctx *c) {
+  const Lattice &L = c->L;
+  if (L.bc_z == 1) {
+    dim3 b(32, 4, 1), g((L.nx + 31) / 32, (L.ny + 3) / 4, 1);
+    k_ghost_init<<<g, b, 0, c->stream>>>(L, c->link, (float)c->prm.u_in, (float)c->prm.c_in,
+                                         (float)c->prm.rho_out, c->fa, c->fb);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(double), c->stream));
+  int rc = launch_observables(c);
+  if (rc) return rc;
+  double h[8];
+  CK(cudaMemcpyAsync(h, c->obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->mc0 = h[2];
+  c->step = 0;
+  c->have_fields = false;
+  return LBM_OK;
+}
+
+int launch_step(lbm_ctx *c) {
+  const Lattice &L = c->L;
+  const dim3 nb = node_block(), ng = node_grid(L);
+  const int slot = (int)(c->step & 1);
+  prof_begin(c, 0);
+  k_density<<<ng, nb, 0, c->stream>>>(L, c->fa, c->link, c->rhoN);
+  prof_end(c);
+  if (c->n_bnd > 0) {
+    const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
+    prof_begin(c, 1);
+    k_color_solid<<<gb, 256, 0, c->stream>>>(L, c->bnd_list, c->n_bnd, c->link, c->rhoN);
+    prof_end(c);
+  }
+  prof_begin(c, 2);
+  k_normal<<<ng, nb, 0, c->stream>>>(L, c->sp, c->rhoN, c->link, c->ns, c->nrm);
+  prof_end(c);
+  if (c->n_bnd > 0) {
+    const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
+    prof_begin(c, 3);
+    k_normal_solid<<<gb, 256, 0, c->stream>>>(L, c->bnd_list, c->n_bnd, c->link, c->nrm);
+    prof_end(c);
+  }
+  prof_begin(c, 4);
+  k_main<<<ng, nb, 0, c->stream>>>(L, c->sp, c->fa, c->fb, c->link, c->nrm, c->acc, slot,
+                                   c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
+  prof_end(c);
+  CK(cudaGetLastError());
+  float *t = c->fa;
+  c->fa = c->fb;
+  c->fb = t;
+  c->step += 1;
+  c->have_fields = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument (dimensions, parameters, sizes or null pointer)";
+    case LBM_ENOMEM: return "device memory allocation failed";
+    case LBM_ECUDA: return "CUDA launch or execution error";
+    case LBM_ENAN: return "non-finite or non-positive density detected";
+    default: return "unknown error code";
+  }
+}
+
+int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out) {
+  if (!geom || !params || !out || !geom->solid) return LBM_EINVAL;
+  if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return LBM_EINVAL;
+  if (geom->bc_z != 0 && geom->bc_z != 1) return LBM_EINVAL;
+  if (geom->bc_z == 1 && geom->nz < 2) return LBM_EINVAL;
+  if (geom->nz > 65535 || geom->ny > 4 * 65535) return LBM_EINVAL;   // grid.z = nz, grid.y = ny / 4
+  int rc = check_params(params);
+  if (rc) return rc;
+  const long long n = (long long)geom->nx * geom->ny * geom->nz;
+  if (n > (1ll << 31) - 1) return LBM_EINVAL;   // node lists are 32-bit
+  long long nfl = 0;
+  for (long long i = 0; i < n; ++i) nfl += geom->solid[i] ? 0 : 1;
+  if (nfl == 0) return LBM_EINVAL;
+
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ENOMEM;
+  cudaGetDevice(&c->device);
+  c->prm = *params;
+  c->stream = (cudaStream_t)params->cuda_stream;
+  Lattice &L = c->L;
+  L.nx = geom->nx;
+  L.ny = geom->ny;
+  L.nz = geom->nz;
+  L.bc_z = geom->bc_z;
+  L.n = n;
+  L.plane = (long long)L.nx * L.ny;
+  L.pstride = L.plane * (L.nz + 2);
+  c->n_fluid = nfl;
+  fill_step_params(c);
+
+  const size_t pop_bytes = (size_t)NPOP * L.pstride * sizeof(float);
+  uint8_t *d_solid = nullptr, *d_react = nullptr;
+  rc = LBM_OK;
+  rc = rc ? rc : dalloc(c, (void **)&c->fa, pop_bytes);
+  rc = rc ? rc : dalloc(c, (void **)&c->fb, pop_bytes);
+  rc = rc ? rc : dalloc(c, (void **)&c->link, n * sizeof(uint32_t));
+  rc = rc ? rc : dalloc(c, (void **)&c->ns, n * sizeof(float4));
+  rc = rc ? rc : dalloc(c, (void **)&c->rhoN, n * sizeof(float));
+  rc = rc ? rc : dalloc(c, (void **)&c->nrm, n * sizeof(float4));
+  rc = rc ? rc : dalloc(c, (void **)&c->acc, 8 * sizeof(double));
+  rc = rc ? rc : dalloc(c, (void **)&c->obs, 8 * sizeof(double));
+  if (!rc && cudaMalloc((void **)&d_solid, n) != cudaSuccess) rc = LBM_ENOMEM;
+  if (!rc && geom->reactive && cudaMalloc((void **)&d_react, n) != cudaSuccess) rc = LBM_ENOMEM;
+  if (rc) {
+    (void)cudaGetLastError();
+    cudaFree(d_solid);
+    cudaFree(d_react);
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  auto fail = [&](int code) {
+    cudaFree(d_solid);
+    cudaFree(d_react);
+    free_all(c);
+    delete c;
+    return code;
+  };
+  if (cudaMemcpy(d_solid, geom->solid, n, cudaMemcpyHostToDevice) != cudaSuccess) return fail(LBM_ECUDA);
+  if (d_react && cudaMemcpy(d_react, geom->reactive, n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LBM_ECUDA);
+  // zero everything once: ghost planes of periodic runs and solid slots stay defined
+  if (cudaMemsetAsync(c->fa, 0, pop_bytes, c->stream) != cudaSuccess) return fail(LBM_ECUDA);
+  if (cudaMemsetAsync(c->fb, 0, pop_bytes, c->stream) != cudaSuccess) return fail(LBM_ECUDA);
+  if (cudaMemsetAsync(c->rhoN, 0, n * sizeof(float), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
+  if (cudaMemsetAsync(c->nrm, 0, n * sizeof(float4), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
+  k_geom<<<node_grid(L), node_block(), 0, c->stream>>>(L, d_solid, d_react, c->link, c->ns);
+  if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
+  // boundary-solid list, built from the device flags in node order
+  std::vector<uint32_t> hlink(n);
+  if (cudaMemcpyAsync(hlink.data(), c->link, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(LBM_ECUDA);
+  cudaFree(d_solid);
+  cudaFree(d_react);
+  d_solid = d_react = nullptr;
+  std::vector<uint32_t> blist;
+  for (long long i = 0; i < n; ++i) {
+    if (hlink[i] & BIT_SOLID_BND) blist.push_back((uint32_t)i);
+    if (hlink[i] & BIT_WALL) c->n_wall++;
+  }
+  c->n_bnd = (long long)blist.size();
+  if (c->n_bnd > 0) {
+    if (dalloc(c, (void **)&c->bnd_list, blist.size() * sizeof(uint32_t))) return fail(LBM_ENOMEM);
+    if (cudaMemcpy(c->bnd_list, blist.data(), blist.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return fail(LBM_ECUDA);
+  }
+  k_init<<<node_grid(L), node_block(), 0, c->stream>>>(L, c->link, nullptr, nullptr, nullptr, nullptr, 1.0f,
+                                                       0.0f, (float)params->c_init, c->fa, c->fb);
+  if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
+  rc = reset_after_state(c);
+  if (rc) return fail(rc);
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int64_t nsteps) {
+  if (!c || nsteps < 0) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    int rc = launch_step(c);
+    if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_observables(lbm_ctx *c, lbm_obs *out) {
+  if (!c || !out) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  int rc = launch_observables(c);
+  if (rc) return rc;
+  double h[8], a[4];
+  CK(cudaMemcpyAsync(h, c->obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof(*out));
+  out->mass_r = h[0];
+  out->mass_p = h[1];
+  out->mass_c = h[2];
+  out->consumed = a[0];
+  out->rate = c->step > 0 ? a[2 + ((c->step - 1) & 1)] : 0.0;
+  out->gas_saturation = h[3] / (double)c->n_fluid;
+  out->flux_in = h[4];
+  out->flux_out = h[5];
+  out->n_bad = (int64_t)h[6];
+  out->step = c->step;
+  out->n_fluid = c->n_fluid;
+  if (c->L.bc_z == 1)
+    out->conversion = out->flux_in != 0.0 ? 1.0 - out->flux_out / out->flux_in : 0.0;
+  else
+    out->conversion = c->mc0 != 0.0 ? out->consumed / c->mc0 : 0.0;
+  return out->n_bad ? LBM_ENAN : LBM_OK;
+}
+
+int lbm_reaction(lbm_ctx *c, double *rate, double *consumed) {
+  if (!c) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  double a[4];
+  CK(cudaMemcpyAsync(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (rate) *rate = c->step > 0 ? a[2 + ((c->step - 1) & 1)] : 0.0;
+  if (consumed) *consumed = a[0];
+  return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx *c, const float *rho_r, const float *rho_p, const float *conc, const float *u) {
+  if (!c || !rho_r || !rho_p || !conc) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  const Lattice &L = c->L;
+  const size_t nb = (size_t)L.n * sizeof(float);
+  float *d = nullptr;
+  const size_t tot = nb * (u ? 6 : 3);
+  if (cudaMalloc((void **)&d, tot) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  int rc = LBM_OK;
+  if (cudaMemcpy(d, rho_r, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy((char *)d + nb, rho_p, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy((char *)d + 2 * nb, conc, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (u && cudaMemcpy((char *)d + 3 * nb, u, 3 * nb, cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = cuda_fail(c, cudaErrorUnknown);
+  if (!rc) {
+    const float *fd = d;
+    k_init<<<node_grid(L), node_block(), 0, c->stream>>>(L, c->link, fd, fd + L.n, fd + 2 * L.n,
+                                                         u ? fd + 3 * L.n : nullptr, 0.f, 0.f, 0.f, c->fa,
+                                                         c->fb);
+    if (cudaGetLastError() != cudaSuccess) rc = cuda_fail(c, cudaErrorLaunchFailure);
+  }
+  if (!rc) rc = reset_after_state(c);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  return rc;
+}
+
+int lbm_get_state(lbm_ctx *c, float *dst, size_t bytes) {
+  if (!c || !dst) return LBM_EINVAL;
+  const Lattice &L = c->L;
+  if (bytes != (size_t)NPOP * L.n * sizeof(float)) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  for (int p = 0; p < NPOP; ++p)
+    CK(cudaMemcpyAsync(dst + (size_t)p * L.n, c->fa + (size_t)p * L.pstride + L.plane, L.n * sizeof(float),
+                       cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *c, const float *src, size_t bytes) {
+  if (!c || !src) return LBM_EINVAL;
+  const Lattice &L = c->L;
+  if (bytes != (size_t)NPOP * L.n * sizeof(float)) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  for (int p = 0; p < NPOP; ++p) {
+    CK(cudaMemcpyAsync(c->fa + (size_t)p * L.pstride + L.plane, src + (size_t)p * L.n, L.n * sizeof(float),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->fb + (size_t)p * L.pstride + L.plane, src + (size_t)p * L.n, L.n * sizeof(float),
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+  return reset_after_state(c);
+}
+
+int lbm_set_debug(lbm_ctx *c, int32_t enable) {
+  if (!c) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  if (enable && !c->dbg_H) {
+    const size_t nb = (size_t)c->L.n * sizeof(float);
+    if (dalloc(c, (void **)&c->dbg_H, nb) || dalloc(c, (void **)&c->dbg_delta, nb)) return LBM_ENOMEM;
+    if (cudaMemset(c->dbg_H, 0, nb) != cudaSuccess || cudaMemset(c->dbg_delta, 0, nb) != cudaSuccess)
+      return cuda_fail(c, cudaErrorUnknown);
+  }
+  c->debug = enable != 0;
+  return LBM_OK;
+}
+
+int lbm_get_field(lbm_ctx *c, int32_t which, float *dst, size_t bytes) {
+  if (!c || !dst) return LBM_EINVAL;
+  if (c->sticky) return c->sticky;
+  cudaSetDevice(c->device);
+  const Lattice &L = c->L;
+  const size_t n = (size_t)L.n;
+  const size_t one = n * sizeof(float);
+  if (which == LBM_FIELD_RHON || which == LBM_FIELD_GRADMAG || which == LBM_FIELD_NN ||
+      which == LBM_FIELD_CURV || which == LBM_FIELD_DELTA) {
+    if (bytes != one) return LBM_EINVAL;
+  } else if (which == LBM_FIELD_NORMAL || which == LBM_FIELD_NS) {
+    if (bytes != 3 * one) return LBM_EINVAL;
+  } else {
+    return LBM_EINVAL;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (which == LBM_FIELD_RHON) {
+    CK(cudaMemcpy(dst, c->rhoN, one, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+  }
+  if (which == LBM_FIELD_CURV || which == LBM_FIELD_DELTA) {
+    if (!c->dbg_H) return LBM_EINVAL;
+    CK(cudaMemcpy(dst, which == LBM_FIELD_CURV ? c->dbg_H : c->dbg_delta, one, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+  }
+  if (which == LBM_FIELD_NN) {
+    std::vector<uint32_t> h(n);
+    CK(cudaMemcpy(h.data(), c->link, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) dst[i] = (float)((h[i] >> NN_SHIFT) & 7u);
+    return LBM_OK;
+  }
+  std::vector<float4> h(n);
+  CK(cudaMemcpy(h.data(), which == LBM_FIELD_NS ? c->ns : c->nrm, n * sizeof(float4), cudaMemcpyDeviceToHost));
+  if (which == LBM_FIELD_GRADMAG) {
+    for (size_t i = 0; i < n; ++i) dst[i] = h[i].w;
+    return LBM_OK;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    dst[i] = h[i].x;
+    dst[n + i] = h[i].y;
+    dst[2 * n + i] = h[i].z;
+  }
+  return LBM_OK;
+}
+
+int lbm_profile(lbm_ctx *c, int32_t max_launches) {
+  if (!c || max_launches < 0) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  const size_t need = (size_t)max_launches * 2;
+  while (c->ev.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  c->ev_kind.assign(c->ev.size() / 2 + 1, 0);
+  c->ev_used = 0;
+  c->profiling = max_launches > 0;
+  return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches, int32_t n) {
+  if (!c || !ms || !launches || n < 1 || n > LBM_NKERNELS) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+    const int k = c->ev_kind[i / 2];
+    if (k < n) {
+      ms[k] += t;
+      launches[k] += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_info(lbm_ctx *c, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd, int64_t *device_bytes) {
+  if (!c) return LBM_EINVAL;
+  if (n_fluid) *n_fluid = c->n_fluid;
+  if (n_wall) *n_wall = c->n_wall;
+  if (n_solid_bnd) *n_solid_bnd = c->n_bnd;
+  if (device_bytes) *device_bytes = (int64_t)c->device_bytes;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,704 @@
+// CUDA kernels of one colour-gradient LB time step (sm_103a, FP32 storage and
+// arithmetic, FP64 reductions).
+//
+// Per step, in order (one launch each):
+//   k_density       pull rho^r, rho^p -> colour function rho^N       (Eq. color_function)
+//   k_color_solid   rho^N at solid nodes next to the fluid           (Eq. color_lattice_weighted_average)
+//   k_normal        gradient, n = +grad/|grad|, wetting              (Eq. finite_difference_scheme,
+//                                                                     Eq. realigned_normal_vectors)
+//   k_normal_solid  n at solid nodes next to the fluid (weighted average of fluid n, renormalised)
+//   k_main          pull all 45 populations, curvature, CSF/EDM force, central-moment collision,
+//                   recolouring, reaction, D3Q7 transport; store; outlet ghost; FP64 sum of delta
+// plus k_geom (once), k_init, k_ghost_init and k_observables.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lattice.cuh"
+
+namespace cglbm {
+
+struct StepParams {
+  float omega_cm;     // 1 - 1/tau (Eq. post_collision_moments)
+  float half_sigma;   // sigma / 2 (Eq. continuum_surface_force)
+  float beta;
+  float cos_th, sin_th;
+  float ax, ay, az;
+  float inv_tau_g;    // 1 / (D / c_s^2 + 1/2), c_s^2 = 1/4 on D3Q7
+  float k_rate, xi, rho_out;
+  int reaction_mode;  // 0: C-mode reaction + D3Q7 transport; 1: paper mode
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float feq19(int i, float rho, float vx, float vy, float vz, float vv) {
+  const float cu = CX[i] * vx + CY[i] * vy + CZ[i] * vz;
+  return W[i] * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * vv);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of NV doubles into global accumulators (one atomic per value per block)
+template <int NV>
+__device__ __forceinline__ void block_accumulate(double (&v)[NV], double *acc) {
+  __shared__ double red[32][NV];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (nthreads + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < nw ? red[lane][k] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0 && s != 0.0) atomicAdd(acc + k, s);
+    }
+  }
+}
+
+// Closed-form T^{-1} k* of Appendix A, Eq. back_transformation_vector, one row
+// per population; rows 6..17 share one pattern per coordinate plane.
+__device__ __forceinline__ void back_transform(float ux, float uy, float uz, float k5, float k6,
+                                               float k7, float k8, float k9, float (&bt)[Q]) {
+  const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+  {  // rows 0, 1: c = (+-1, 0, 0)
+    const float A = ux2 - uy2 - uz2 + 1.0f;
+    const float P = k5 * (1.0f / 3.0f) + k6 * (1.0f / 6.0f);
+    const float R = uy * k7 + uz * k8;
+    bt[0] = (A + ux) * P - (2.0f * ux + 1.0f) * R;
+    bt[1] = (A - ux) * P - (2.0f * ux - 1.0f) * R;
+  }
+  {  // rows 2, 3: c = (0, +-1, 0)
+    const float B = ux2 - uy2 + uz2 - 1.0f;
+    const float P = (k5 - k6) * (1.0f / 6.0f);
+    const float R = ux * k7 + uz * k9;
+    bt[2] = (B - uy) * P - (2.0f * uy + 1.0f) * R;
+    bt[3] = (B + uy) * P - (2.0f * uy - 1.0f) * R;
+  }
+  {  // rows 4, 5: c = (0, 0, +-1)
+    const float Cc = ux2 + uy2 - uz2 - 1.0f;
+    const float P = k5 * (1.0f / 6.0f) + k6 * (1.0f / 3.0f);
+    const float R = ux * k8 + uy * k9;
+    bt[4] = (Cc - uz) * P - (2.0f * uz + 1.0f) * R;
+    bt[5] = (Cc + uz) * P - (2.0f * uz - 1.0f) * R;
+  }
+  constexpr float T12 = 1.0f / 12.0f;
+  // rows c = (a, b, 0): 6 (1,1), 7 (1,-1), 10 (-1,1), 11 (-1,-1)
+  {
+    const float uxuy12 = 12.0f * ux * uy;
+    const int ia[4] = {6, 7, 10, 11};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = ia[m];
+      const float a = (float)CX[i], b = (float)CY[i];
+      const float c5 = -ux2 - a * ux + 2.0f * uy2 + 2.0f * b * uy;
+      const float c6 = ux2 + a * ux + uy2 + b * uy;
+      const float c7 = uxuy12 + 6.0f * b * ux + 6.0f * a * uy + 3.0f * a * b;
+      bt[i] = (c5 * k5 + c6 * k6 + c7 * k7) * T12;
+    }
+  }
+  // rows c = (a, 0, b): 8 (1,1), 9 (1,-1), 12 (-1,1), 13 (-1,-1)
+  {
+    const float uxuz12 = 12.0f * ux * uz;
+    const int ia[4] = {8, 9, 12, 13};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = ia[m];
+      const float a = (float)CX[i], b = (float)CZ[i];
+      const float c5 = -ux2 - a * ux + 2.0f * uz2 + 2.0f * b * uz;
+      const float c6 = -2.0f * ux2 - 2.0f * a * ux + uz2 + b * uz;
+      const float c8 = uxuz12 + 6.0f * b * ux + 6.0f * a * uz + 3.0f * a * b;
+      bt[i] = (c5 * k5 + c6 * k6 + c8 * k8) * T12;
+    }
+  }
+  // rows c = (0, a, b): 14 (1,1), 15 (1,-1), 16 (-1,1), 17 (-1,-1)
+  {
+    const float uyuz12 = 12.0f * uy * uz;
+    const int ia[4] = {14, 15, 16, 17};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = ia[m];
+      const float a = (float)CY[i], b = (float)CZ[i];
+      const float c5 = -uy2 - a * uy - uz2 - b * uz;
+      const float c6 = -2.0f * uy2 - 2.0f * a * uy + uz2 + b * uz;
+      const float c9 = uyuz12 + 6.0f * b * uy + 6.0f * a * uz + 3.0f * a * b;
+      bt[i] = (c5 * k5 + c6 * k6 + c9 * k9) * T12;
+    }
+  }
+  bt[18] = (-2.0f * ux2 + uy2 + uz2) * k5 * (1.0f / 3.0f) + (-ux2 - uy2 + 2.0f * uz2) * k6 * (1.0f / 3.0f) +
+           4.0f * (ux * uy * k7 + ux * uz * k8 + uy * uz * k9);
+}
+
+// Outlet ghost plane (column mode) from the post-collision populations of a
+// fluid node of plane nz - 1: non-equilibrium extrapolation to rho_out, split
+// by the node's colour ratio; g copied.  Writes the populations with c_z = -1.
+__device__ __forceinline__ void write_outlet_ghost(const Lattice &L, float *__restrict__ f, int x, int y,
+                                                   const float (&fr)[Q], const float (&fp)[Q],
+                                                   float g5, float rho_out) {
+  float rho = 0.f, rr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float m = fr[i] + fp[i];
+    rho += m;
+    rr += fr[i];
+    jx += CX[i] * m;
+    jy += CY[i] * m;
+    jz += CZ[i] * m;
+  }
+  const float inv = 1.0f / rho;
+  const float vx = jx * inv, vy = jy * inv, vz = jz * inv;
+  const float vv = vx * vx + vy * vy + vz * vz;
+  const float psi = rr * inv;
+  const int zp = L.nz + 1;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (CZ[i] != -1) continue;
+    const float corr = feq19(i, rho_out - rho, vx, vy, vz, vv);
+    f[pidx(L, i, zp, y, x)] = fr[i] + psi * corr;
+    f[pidx(L, Q + i, zp, y, x)] = fp[i] + (1.0f - psi) * corr;
+  }
+  f[pidx(L, 2 * Q + 5, zp, y, x)] = g5;
+}
+
+// ---------------------------------------------------------------------------
+// one-time geometry: link bits, NN, r, wall / boundary flags, solid normal
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float omega8(int e2) {
+  // Eq. eigth_order_weight_function
+  switch (e2) {
+    case 1: return 4.0f / 45.0f;
+    case 2: return 1.0f / 21.0f;
+    case 3: return 2.0f / 105.0f;
+    case 4: return 5.0f / 504.0f;
+    case 5: return 1.0f / 315.0f;
+    case 6: return 1.0f / 630.0f;
+    case 8: return 1.0f / 5040.0f;
+    default: return 0.0f;
+  }
+}
+
+__device__ __forceinline__ bool solid_at(const Lattice &L, const uint8_t *__restrict__ solid, int x, int y,
+                                         int z) {
+  x = ((x % L.nx) + L.nx) % L.nx;
+  y = ((y % L.ny) + L.ny) % L.ny;
+  if (L.bc_z == 0)
+    z = ((z % L.nz) + L.nz) % L.nz;
+  else
+    z = z < 0 ? 0 : (z >= L.nz ? L.nz - 1 : z);
+  return solid[nidx(L, x, y, z)] != 0;
+}
+
+__global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8_t *__restrict__ reactive,
+                       uint32_t *__restrict__ link, float4 *__restrict__ ns) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long node = nidx(L, x, y, z);
+  uint32_t bits = 0;
+  float4 nsv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (solid[node]) {
+    bits = BIT_SOLID;
+    for (int i = 0; i < Q - 1; ++i)
+      if (!solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i])) bits |= BIT_SOLID_BND;
+  } else {
+    // bounce-back links: the pull source x - c_i is solid (column ghosts are fluid)
+    for (int i = 0; i < Q - 1; ++i) {
+      const int sz = z - CZ[i];
+      if (L.bc_z == 1 && (sz < 0 || sz >= L.nz)) continue;
+      if (solid_at(L, solid, x - CX[i], y - CY[i], sz)) bits |= 1u << i;
+    }
+    bool wall = false;
+    for (int i = 0; i < Q - 1; ++i) wall |= solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i]);
+    // Eq. nearest_solid_neighbors
+    int nn = 0;
+    for (int i = 0; i < 6; ++i) nn += solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i]) ? 1 : 0;
+    bits |= (uint32_t)nn << NN_SHIFT;
+    const bool r = reactive ? (reactive[node] != 0) : (nn >= 1);
+    if (r) bits |= BIT_REACTIVE;
+    if (wall) {
+      bits |= BIT_WALL;
+      // Eq. normal_vector_solid over the 92 vectors with |e|^2 in {1,..,6,8}
+      float sx = 0.f, sy = 0.f, sz = 0.f;
+      for (int ez = -2; ez <= 2; ++ez)
+        for (int ey = -2; ey <= 2; ++ey)
+          for (int ex = -2; ex <= 2; ++ex) {
+            const float w = omega8(ex * ex + ey * ey + ez * ez);
+            if (w == 0.f) continue;
+            if (solid_at(L, solid, x + ex, y + ey, z + ez)) {
+              sx += w * ex;
+              sy += w * ey;
+              sz += w * ez;
+            }
+          }
+      const float m = sqrtf(sx * sx + sy * sy + sz * sz);
+      if (m > 0.f) {
+        bits |= BIT_NS_OK;
+        nsv = make_float4(sx / m, sy / m, sz / m, 0.f);
+      }
+    }
+  }
+  link[node] = bits;
+  ns[node] = nsv;
+}
+
+// ---------------------------------------------------------------------------
+// start state
+// ---------------------------------------------------------------------------
+// f^k = f^eq(rho^k, u), g = g^eq(C, u); fields may be null (uniform defaults)
+__global__ void k_init(Lattice L, const uint32_t *__restrict__ link, const float *__restrict__ rho_r,
+                       const float *__restrict__ rho_p, const float *__restrict__ conc,
+                       const float *__restrict__ u, float rr0, float rp0, float c0, float *__restrict__ fa,
+                       float *__restrict__ fb) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long node = nidx(L, x, y, z);
+  const bool fluid = !(link[node] & BIT_SOLID);
+  const float rr = fluid ? (rho_r ? rho_r[node] : rr0) : 0.f;
+  const float rp = fluid ? (rho_p ? rho_p[node] : rp0) : 0.f;
+  const float cc = fluid ? (conc ? conc[node] : c0) : 0.f;
+  const float ux = (fluid && u) ? u[node] : 0.f;
+  const float uy = (fluid && u) ? u[L.n + node] : 0.f;
+  const float uz = (fluid && u) ? u[2 * L.n + node] : 0.f;
+  const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float a = feq19(i, rr, ux, uy, uz, uu), b = feq19(i, rp, ux, uy, uz, uu);
+    fa[pidx(L, i, z + 1, y, x)] = a;
+    fb[pidx(L, i, z + 1, y, x)] = a;
+    fa[pidx(L, Q + i, z + 1, y, x)] = b;
+    fb[pidx(L, Q + i, z + 1, y, x)] = b;
+  }
+#pragma unroll
+  for (int j = 0; j < Q7; ++j) {
+    const int d = GDIR[j];
+    const float gv = W7[j] * cc * (1.0f + 4.0f * (CX[d] * ux + CY[d] * uy + CZ[d] * uz));
+    fa[pidx(L, 2 * Q + j, z + 1, y, x)] = gv;
+    fb[pidx(L, 2 * Q + j, z + 1, y, x)] = gv;
+  }
+}
+
+// Column ghost planes of both buffers: constant inlet (z = -1): f^r = f^eq(1, u_in z),
+// f^p = 0, g = g^eq(c_in, u_in z); outlet (z = nz) from plane nz - 1 of buffer fa
+// (the current state), resting reactant equilibrium above solid nodes.
+__global__ void k_ghost_init(Lattice L, const uint32_t *__restrict__ link, float u_in, float c_in,
+                             float rho_out, float *__restrict__ fa, float *__restrict__ fb) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.nx || y >= L.ny) return;
+  const float uu = u_in * u_in;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (CZ[i] != 1) continue;
+    const float v = feq19(i, 1.0f, 0.f, 0.f, u_in, uu);
+    fa[pidx(L, i, 0, y, x)] = v;
+    fb[pidx(L, i, 0, y, x)] = v;
+    fa[pidx(L, Q + i, 0, y, x)] = 0.f;
+    fb[pidx(L, Q + i, 0, y, x)] = 0.f;
+  }
+  const float g4 = W7[4] * c_in * (1.0f + 4.0f * u_in);
+  fa[pidx(L, 2 * Q + 4, 0, y, x)] = g4;
+  fb[pidx(L, 2 * Q + 4, 0, y, x)] = g4;
+  const int z = L.nz - 1;
+  const long long node = nidx(L, x, y, z);
+  if (link[node] & BIT_SOLID) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (CZ[i] != -1) continue;
+      const float v = W[i] * rho_out;
+      fa[pidx(L, i, L.nz + 1, y, x)] = v;
+      fb[pidx(L, i, L.nz + 1, y, x)] = v;
+      fa[pidx(L, Q + i, L.nz + 1, y, x)] = 0.f;
+      fb[pidx(L, Q + i, L.nz + 1, y, x)] = 0.f;
+    }
+    fa[pidx(L, 2 * Q + 5, L.nz + 1, y, x)] = 0.f;
+    fb[pidx(L, 2 * Q + 5, L.nz + 1, y, x)] = 0.f;
+  } else {
+    float fr[Q], fp[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      fr[i] = fa[pidx(L, i, z + 1, y, x)];
+      fp[i] = fa[pidx(L, Q + i, z + 1, y, x)];
+    }
+    write_outlet_ghost(L, fa, x, y, fr, fp, fa[pidx(L, 2 * Q + 5, z + 1, y, x)], rho_out);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a1 + a2: colour function from the pulled populations
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_density(Lattice L, const float *__restrict__ f,
+                                                 const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long node = nidx(L, x, y, z);
+  const uint32_t lk = link[node];
+  if (lk & BIT_SOLID) return;
+  Stencil S;
+  S.init(L, x, y, z);
+  int zp[3];
+  pull_planes(L, z, zp);
+  float rr = 0.f, rp = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    long long src;
+    int pr, pp;
+    if ((lk >> i) & 1u) {  // halfway bounce-back: f_i(x) = f*_opp(i)(x)
+      src = pidx(L, 0, z + 1, y, x);
+      pr = OPP[i];
+    } else {
+      src = pidx(L, 0, zp[1 - CZ[i]], S.ys[1 - CY[i]], S.xs[1 - CX[i]]);
+      pr = i;
+    }
+    pp = Q + pr;
+    rr += f[src + (long long)pr * L.pstride];
+    rp += f[src + (long long)pp * L.pstride];
+  }
+  rhoN[node] = (rr - rp) / (rr + rp);
+}
+
+// a3: Eq. color_lattice_weighted_average at solid nodes next to the fluid
+__global__ void k_color_solid(Lattice L, const uint32_t *__restrict__ list, long long count,
+                              const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const long long s = list[t];
+  const int z = (int)(s / L.plane);
+  const long long rem = s - (long long)z * L.plane;
+  const int y = (int)(rem / L.nx), x = (int)(rem - (long long)y * L.nx);
+  Stencil S;
+  S.init(L, x, y, z);
+  float num = 0.f, den = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    const long long nb = S.nb(L, CX[i], CY[i], CZ[i]);
+    if (!(link[nb] & BIT_SOLID)) {
+      num += W[i] * rhoN[nb];
+      den += W[i];
+    }
+  }
+  rhoN[s] = den > 0.f ? num / den : 0.f;
+}
+
+// a4 + a5: isotropic gradient, normal, Akai wetting at wall nodes
+__global__ void __launch_bounds__(256) k_normal(Lattice L, StepParams P, const float *__restrict__ rhoN,
+                                                const uint32_t *__restrict__ link, const float4 *__restrict__ ns,
+                                                float4 *__restrict__ nrm) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long node = nidx(L, x, y, z);
+  const uint32_t lk = link[node];
+  if (lk & BIT_SOLID) return;
+  Stencil S;
+  S.init(L, x, y, z);
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    const float v = 3.0f * W[i] * rhoN[S.nb(L, CX[i], CY[i], CZ[i])];
+    gx += CX[i] * v;
+    gy += CY[i] * v;
+    gz += CZ[i] * v;
+  }
+  const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
+  float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
+  if (gm >= GRAD_EPS) {
+    const float inv = 1.0f / gm;
+    nx_ = gx * inv;
+    ny_ = gy * inv;
+    nz_ = gz * inv;
+    if ((lk & BIT_WALL) && (lk & BIT_NS_OK)) {
+      const float4 s = ns[node];
+      const float c = s.x * nx_ + s.y * ny_ + s.z * nz_;          // cos(theta')
+      const float tx = nx_ - c * s.x, ty = ny_ - c * s.y, tz = nz_ - c * s.z;
+      const float st2 = tx * tx + ty * ty + tz * tz;              // sin^2(theta')
+      if (st2 >= SIN2_EPS) {
+        const float st = sqrtf(st2);
+        const float a_s = P.sin_th * c / st, a_n = P.sin_th / st;
+        // n_+ and n_- of Eq. realigned_normal_vectors
+        const float px = (P.cos_th - a_s) * s.x + a_n * nx_;
+        const float py = (P.cos_th - a_s) * s.y + a_n * ny_;
+        const float pz = (P.cos_th - a_s) * s.z + a_n * nz_;
+        const float mx = (P.cos_th + a_s) * s.x - a_n * nx_;
+        const float my = (P.cos_th + a_s) * s.y - a_n * ny_;
+        const float mz = (P.cos_th + a_s) * s.z - a_n * nz_;
+        const float dp = (px - nx_) * (px - nx_) + (py - ny_) * (py - ny_) + (pz - nz_) * (pz - nz_);
+        const float dm = (mx - nx_) * (mx - nx_) + (my - ny_) * (my - ny_) + (mz - nz_) * (mz - nz_);
+        if (dp <= dm) {
+          nx_ = px; ny_ = py; nz_ = pz;
+        } else {
+          nx_ = mx; ny_ = my; nz_ = mz;
+        }
+      }
+    }
+  }
+  nrm[node] = make_float4(nx_, ny_, nz_, gm);
+}
+
+// n at solid nodes next to the fluid: lattice-weighted average of the fluid
+// neighbours' wetted n, renormalised (needed by the curvature stencil)
+__global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, long long count,
+                               const uint32_t *__restrict__ link, float4 *__restrict__ nrm) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const long long s = list[t];
+  const int z = (int)(s / L.plane);
+  const long long rem = s - (long long)z * L.plane;
+  const int y = (int)(rem / L.nx), x = (int)(rem - (long long)y * L.nx);
+  Stencil S;
+  S.init(L, x, y, z);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    const long long nb = S.nb(L, CX[i], CY[i], CZ[i]);
+    if (!(link[nb] & BIT_SOLID)) {
+      const float4 v = nrm[nb];
+      ax += W[i] * v.x;
+      ay += W[i] * v.y;
+      az += W[i] * v.z;
+    }
+  }
+  const float m = sqrtf(ax * ax + ay * ay + az * az);
+  if (m >= GRAD_EPS) {
+    const float inv = 1.0f / m;
+    nrm[s] = make_float4(ax * inv, ay * inv, az * inv, 0.f);
+  } else {
+    nrm[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a1, a2, a6 - a10: the fused main update
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const float *__restrict__ fin,
+                                              float *__restrict__ fout, const uint32_t *__restrict__ link,
+                                              const float4 *__restrict__ nrm, double *__restrict__ acc,
+                                              int slot, float *__restrict__ dbg_H, float *__restrict__ dbg_delta) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  double dsum = 0.0;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    acc[2 + (slot ^ 1)] = 0.0;   // clear the other per-step slot for the next step
+  const bool inside = x < L.nx && y < L.ny;
+  const long long node = inside ? nidx(L, x, y, z) : 0;
+  const uint32_t lk = inside ? link[node] : BIT_SOLID;
+  if (!(lk & BIT_SOLID)) {
+    Stencil S;
+    S.init(L, x, y, z);
+    int zp[3];
+    pull_planes(L, z, zp);
+    // a1: pull with bounce-back
+    float fr[Q], fp[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      long long src;
+      int pr;
+      if ((lk >> i) & 1u) {
+        src = pidx(L, 0, z + 1, y, x);
+        pr = OPP[i];
+      } else {
+        src = pidx(L, 0, zp[1 - CZ[i]], S.ys[1 - CY[i]], S.xs[1 - CX[i]]);
+        pr = i;
+      }
+      fr[i] = fin[src + (long long)pr * L.pstride];
+      fp[i] = fin[src + (long long)(Q + pr) * L.pstride];
+    }
+    float g[Q7];
+    if (P.reaction_mode == 0) {
+#pragma unroll
+      for (int j = 0; j < Q7; ++j) {
+        const int d = GDIR[j];
+        long long src;
+        int pj;
+        if ((lk >> d) & 1u) {
+          src = pidx(L, 0, z + 1, y, x);
+          pj = GOPP[j];
+        } else {
+          src = pidx(L, 0, zp[1 - CZ[d]], S.ys[1 - CY[d]], S.xs[1 - CX[d]]);
+          pj = j;
+        }
+        g[j] = fin[src + (long long)(2 * Q + pj) * L.pstride];
+      }
+    }
+    // a2: moments
+    float rr = 0.f, rp = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      rr += fr[i];
+      rp += fp[i];
+      const float m = fr[i] + fp[i];
+      fr[i] = m;   // fr now holds f^m
+      if (CX[i]) jx += CX[i] * m;
+      if (CY[i]) jy += CY[i] * m;
+      if (CZ[i]) jz += CZ[i] * m;
+      if (CX[i]) pxx += m;
+      if (CY[i]) pyy += m;
+      if (CZ[i]) pzz += m;
+      if (CX[i] && CY[i]) pxy += CX[i] * CY[i] * m;
+      if (CX[i] && CZ[i]) pxz += CX[i] * CZ[i] * m;
+      if (CY[i] && CZ[i]) pyz += CY[i] * CZ[i] * m;
+    }
+    const float rho = rr + rp;
+    const float inv_rho = 1.0f / rho;
+    const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    // a6: curvature H = -sum_ab (delta_ab - n_a n_b) d_a n_b
+    const float4 nme = nrm[node];
+    const float gm = nme.w;
+    float H = 0.f;
+    if (gm >= GRAD_EPS) {
+      float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int i = 0; i < Q - 1; ++i) {
+        const float4 v = nrm[S.nb(L, CX[i], CY[i], CZ[i])];
+        const float w3 = 3.0f * W[i];
+        if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
+        if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
+        if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
+      }
+      const float n3[3] = {nme.x, nme.y, nme.z};
+      float proj = d[0][0] + d[1][1] + d[2][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) proj -= n3[a] * n3[b] * d[a][b];
+      H = -proj;
+    }
+    // a7: du = (sigma/2) H |grad rho^N| n / rho^m + a (same for both components)
+    const float fs = P.half_sigma * H * gm * inv_rho;
+    const float dux = fs * nme.x + P.ax, duy = fs * nme.y + P.ay, duz = fs * nme.z + P.az;
+    // a8: central moments k5..k9 of f^m about u (Eq. post_collision_moments)
+    const float k5 = P.omega_cm * ((pxx - pyy) - rho * (ux * ux - uy * uy));
+    const float k6 = P.omega_cm * ((pyy - pzz) - rho * (uy * uy - uz * uz));
+    const float k7 = P.omega_cm * (pxy - rho * ux * uy);
+    const float k8 = P.omega_cm * (pxz - rho * ux * uz);
+    const float k9 = P.omega_cm * (pyz - rho * uy * uz);
+    float bt[Q];
+    back_transform(ux, uy, uz, k5, k6, k7, k8, k9, bt);
+    const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
+    const float vv = vx * vx + vy * vy + vz * vz;
+    // a10: reaction amount (explicit Euler, post-streaming densities)
+    const float psi = rr * inv_rho;
+    float delta = 0.f;
+    const uint32_t nn = (lk >> NN_SHIFT) & 7u;
+    float conc = 0.f;
+    if (P.reaction_mode == 0) {
+#pragma unroll
+      for (int j = 0; j < Q7; ++j) conc += g[j];
+      if (lk & BIT_REACTIVE) delta = fminf(fminf(P.k_rate * (float)nn * conc * psi, conc), rr);
+    } else {
+      if (lk & BIT_REACTIVE) delta = fminf(P.xi * (float)nn, 1.0f) * rr;
+    }
+    delta = fmaxf(delta, 0.f);
+    // a9: recolouring + reaction transfer; fr <- f^r*, fp <- f^p*
+    const float Brec = P.beta * rr * rp * inv_rho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
+      const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
+      const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
+      fr[i] = r_star;
+      fp[i] = fm_star - r_star;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      fout[pidx(L, i, z + 1, y, x)] = fr[i];
+      fout[pidx(L, Q + i, z + 1, y, x)] = fp[i];
+    }
+    float g5 = 0.f;
+    if (P.reaction_mode == 0) {
+      // D3Q7 BGK of C advected by the physical velocity u + du/2, minus the reacted amount
+      const float wx = ux + 0.5f * dux, wy = uy + 0.5f * duy, wz = uz + 0.5f * duz;
+#pragma unroll
+      for (int j = 0; j < Q7; ++j) {
+        const int dd = GDIR[j];
+        const float geq = W7[j] * conc * (1.0f + 4.0f * (CX[dd] * wx + CY[dd] * wy + CZ[dd] * wz));
+        const float gs = g[j] + (geq - g[j]) * P.inv_tau_g - W7[j] * delta;
+        fout[pidx(L, 2 * Q + j, z + 1, y, x)] = gs;
+        if (j == 5) g5 = gs;
+      }
+    }
+    if (L.bc_z == 1 && z == L.nz - 1) {
+      if (P.reaction_mode != 0) g5 = fin[pidx(L, 2 * Q + 5, z + 1, y, x)];
+      write_outlet_ghost(L, fout, x, y, fr, fp, g5, P.rho_out);
+    }
+    if (dbg_H) dbg_H[node] = H;
+    if (dbg_delta) dbg_delta[node] = delta;
+    dsum = (double)delta;
+  }
+  // FP64 block sum of delta -> cumulative total acc[0] and this step's slot acc[2 + slot]
+  __shared__ double red[32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  dsum = warp_sum(dsum);
+  if ((tid & 31) == 0) red[tid >> 5] = dsum;
+  __syncthreads();
+  if (tid < 32) {
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    double s = tid < nw ? red[tid] : 0.0;
+    s = warp_sum(s);
+    if (tid == 0 && s != 0.0) {
+      atomicAdd(acc + 0, s);
+      atomicAdd(acc + 2 + slot, s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a11: observables of the stored state (FP64 block reductions)
+// ---------------------------------------------------------------------------
+// acc layout: 0 mass_r, 1 mass_p, 2 mass_c, 3 sum (1 - rho^N)/2, 4 flux_in, 5 flux_out, 6 n_bad
+__global__ void k_observables(Lattice L, const float *__restrict__ f, const uint32_t *__restrict__ link,
+                              double *__restrict__ acc) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  const bool inside = x < L.nx && y < L.ny;
+  const long long node = inside ? nidx(L, x, y, z) : 0;
+  if (inside && !(link[node] & BIT_SOLID)) {
+    double rr = 0.0, rp = 0.0, cc = 0.0, jz = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double a = f[pidx(L, i, z + 1, y, x)], b = f[pidx(L, Q + i, z + 1, y, x)];
+      rr += a;
+      rp += b;
+      if (CZ[i]) jz += CZ[i] * (a + b);
+    }
+#pragma unroll
+    for (int j = 0; j < Q7; ++j) cc += f[pidx(L, 2 * Q + j, z + 1, y, x)];
+    const double rho = rr + rp;
+    v[0] = rr;
+    v[1] = rp;
+    v[2] = cc;
+    const bool bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(cc);
+    if (!bad) {
+      v[3] = 0.5 * (1.0 - (rr - rp) / rho);
+      if (z == 0) v[4] = jz / rho * cc;
+      if (z == L.nz - 1) v[5] = jz / rho * cc;
+    }
+    v[6] = bad ? 1.0 : 0.0;
+  }
+  block_accumulate<7>(v, acc);
+}
+
+}  // namespace cglbm

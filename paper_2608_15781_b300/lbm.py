@@ -1,0 +1,289 @@
+"""Thin ctypes binding of the C ABI in ``include/cglbm.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libcglbm.so``; this module
+only converts NumPy arrays and dataclasses to the C structures.  If the
+library is missing or fails to load, the calls raise ``LbmError`` -- there is
+no CPU fallback.
+
+Functions carry the C names (``lbm_create``, ``lbm_step``, ``lbm_observables``,
+...); ``Lattice`` bundles them for convenience.  Arrays use the library's
+layout: lattice fields are (nz, ny, nx) with x fastest, populations are
+(45, nz, ny, nx) ordered f^r_0..18, f^p_0..18, g_0..6.
+"""
+import ctypes
+import dataclasses
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcglbm.so")
+NPOP = 45
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN = 0, -1, -2, -3, -4
+FIELD_RHON, FIELD_NORMAL, FIELD_GRADMAG, FIELD_NS, FIELD_NN, FIELD_CURV, FIELD_DELTA = range(7)
+KERNEL_NAMES = ("density", "color_solid", "normal", "normal_solid", "main", "observables")
+
+# exported symbols (kept in sync with include/cglbm.h; the CPU tests check both)
+SYMBOLS = (
+    "lbm_create", "lbm_step", "lbm_observables", "lbm_reaction", "lbm_init_fields", "lbm_get_state",
+    "lbm_set_state", "lbm_get_field", "lbm_set_debug", "lbm_profile", "lbm_profile_read",
+    "lbm_info", "lbm_destroy", "lbm_strerror",
+)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = _strerror(code) if _lib is not None else f"error {code}"
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class _Geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("solid", ctypes.c_void_p), ("reactive", ctypes.c_void_p), ("bc_z", ctypes.c_int32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
+                ("theta_deg", ctypes.c_double), ("accel", ctypes.c_double * 3),
+                ("diffusivity", ctypes.c_double), ("k_rate", ctypes.c_double), ("c_init", ctypes.c_double),
+                ("c_in", ctypes.c_double), ("u_in", ctypes.c_double), ("rho_out", ctypes.c_double),
+                ("xi", ctypes.c_double), ("reaction_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class _Obs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("mass_r", "mass_p", "mass_c", "consumed", "rate", "conversion",
+                                               "gas_saturation", "flux_in", "flux_out")] + \
+               [(n, ctypes.c_int64) for n in ("step", "n_fluid", "n_bad")]
+
+
+@dataclass
+class Params:
+    """Physical and numerical parameters (lattice units); mirrors ``lbm_params``."""
+    tau: float = 1.0
+    sigma: float = 0.01
+    beta: float = 0.7
+    theta_deg: float = 90.0
+    accel: tuple = (0.0, 0.0, 0.0)
+    diffusivity: float = 0.05
+    k_rate: float = 1e-3
+    c_init: float = 1.0
+    c_in: float = 1.0
+    u_in: float = 0.0
+    rho_out: float = 1.0
+    xi: float = 1.0
+    reaction_mode: int = 0
+    storage: int = 0
+
+    def to_c(self, stream=None):
+        p = _Params()
+        for f in dataclasses.fields(self):
+            if f.name == "accel":
+                for a in range(3):
+                    p.accel[a] = float(self.accel[a])
+            else:
+                setattr(p, f.name, getattr(self, f.name))
+        p.cuda_stream = stream
+        return p
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load ``libcglbm.so`` (once).  Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LbmError(LBM_EINVAL, f"CUDA library not built: {path} (run python -m paper_2608_15781_b300.build)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "lbm_create": (ctypes.c_int, [ctypes.POINTER(_Geometry), ctypes.POINTER(_Params), ctypes.POINTER(P)]),
+        "lbm_step": (ctypes.c_int, [P, I64]),
+        "lbm_observables": (ctypes.c_int, [P, ctypes.POINTER(_Obs)]),
+        "lbm_reaction": (ctypes.c_int, [P, P, P]),
+        "lbm_init_fields": (ctypes.c_int, [P, P, P, P, P]),
+        "lbm_get_state": (ctypes.c_int, [P, P, SZ]),
+        "lbm_set_state": (ctypes.c_int, [P, P, SZ]),
+        "lbm_get_field": (ctypes.c_int, [P, I32, P, SZ]),
+        "lbm_set_debug": (ctypes.c_int, [P, I32]),
+        "lbm_profile": (ctypes.c_int, [P, I32]),
+        "lbm_profile_read": (ctypes.c_int, [P, P, P, I32]),
+        "lbm_info": (ctypes.c_int, [P, P, P, P, P]),
+        "lbm_destroy": (None, [P]),
+        "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _strerror(code):
+    return _lib.lbm_strerror(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != LBM_OK:
+        raise LbmError(rc, what)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+# --------------------------------------------------------------------------- C-named calls
+def lbm_create(solid, params, reactive=None, bc_z=0, stream=None):
+    """Create a context for the (nz, ny, nx) mask ``solid``; returns the opaque handle."""
+    lib = load_library()
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    if solid.ndim != 3:
+        raise LbmError(LBM_EINVAL, "solid must be a (nz, ny, nx) array")
+    nz, ny, nx = solid.shape
+    react = None if reactive is None else np.ascontiguousarray(reactive, dtype=np.uint8)
+    if react is not None and react.shape != solid.shape:
+        raise LbmError(LBM_EINVAL, "reactive mask shape")
+    g = _Geometry(nx, ny, nz, solid.ctypes.data, react.ctypes.data if react is not None else None, int(bc_z))
+    p = params.to_c(stream)
+    h = ctypes.c_void_p()
+    _check(lib.lbm_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_step(ctx, nsteps):
+    _check(load_library().lbm_step(ctx, int(nsteps)), "lbm_step")
+
+
+def lbm_observables(ctx, allow_nan=False):
+    o = _Obs()
+    rc = load_library().lbm_observables(ctx, ctypes.byref(o))
+    if rc != LBM_OK and not (allow_nan and rc == LBM_ENAN):
+        _check(rc, "lbm_observables")
+    return {n: getattr(o, n) for n, _ in _Obs._fields_}
+
+
+def lbm_reaction(ctx):
+    """(rate, consumed): the last step's and the cumulative sum of the reaction amounts."""
+    r, c = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().lbm_reaction(ctx, ctypes.byref(r), ctypes.byref(c)), "lbm_reaction")
+    return r.value, c.value
+
+
+def lbm_init_fields(ctx, rho_r, rho_p, conc, u=None):
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (rho_r, rho_p, conc)]
+    ua = None if u is None else np.ascontiguousarray(u, dtype=np.float32)
+    _check(load_library().lbm_init_fields(ctx, *[_ptr(a) for a in arrs], _ptr(ua)), "lbm_init_fields")
+
+
+def lbm_get_state(ctx, shape):
+    nz, ny, nx = shape
+    out = np.empty((NPOP, nz, ny, nx), dtype=np.float32)
+    _check(load_library().lbm_get_state(ctx, _ptr(out), out.nbytes), "lbm_get_state")
+    return out
+
+
+def lbm_set_state(ctx, f):
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    _check(load_library().lbm_set_state(ctx, _ptr(f), f.nbytes), "lbm_set_state")
+
+
+def lbm_get_field(ctx, which, shape):
+    nz, ny, nx = shape
+    comps = 3 if which in (FIELD_NORMAL, FIELD_NS) else 1
+    out = np.empty((comps, nz, ny, nx), dtype=np.float32)
+    _check(load_library().lbm_get_field(ctx, int(which), _ptr(out), out.nbytes), "lbm_get_field")
+    return out if comps == 3 else out[0]
+
+
+def lbm_set_debug(ctx, enable):
+    _check(load_library().lbm_set_debug(ctx, int(bool(enable))), "lbm_set_debug")
+
+
+def lbm_profile(ctx, max_launches):
+    _check(load_library().lbm_profile(ctx, int(max_launches)), "lbm_profile")
+
+
+def lbm_profile_read(ctx):
+    ms = np.zeros(len(KERNEL_NAMES), dtype=np.float64)
+    n = np.zeros(len(KERNEL_NAMES), dtype=np.int64)
+    _check(load_library().lbm_profile_read(ctx, _ptr(ms), _ptr(n), len(KERNEL_NAMES)), "lbm_profile_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+
+def lbm_info(ctx):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load_library().lbm_info(ctx, *[ctypes.byref(a) for a in v]), "lbm_info")
+    return dict(n_fluid=v[0].value, n_wall=v[1].value, n_solid_bnd=v[2].value, device_bytes=v[3].value)
+
+
+def lbm_destroy(ctx):
+    if ctx is not None and ctx.value:
+        load_library().lbm_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- convenience
+class Lattice:
+    """One lattice on the current CUDA device, driven through the C ABI."""
+
+    def __init__(self, solid, params, reactive=None, bc_z=0, stream=None):
+        self.shape = tuple(np.shape(solid))
+        self.params = params
+        self.bc_z = bc_z
+        self.ctx = lbm_create(solid, params, reactive=reactive, bc_z=bc_z, stream=stream)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def observables(self, allow_nan=False):
+        return lbm_observables(self.ctx, allow_nan=allow_nan)
+
+    def reaction(self):
+        return lbm_reaction(self.ctx)
+
+    def init_fields(self, rho_r, rho_p, conc, u=None):
+        lbm_init_fields(self.ctx, rho_r, rho_p, conc, u)
+
+    def get_state(self):
+        return lbm_get_state(self.ctx, self.shape)
+
+    def set_state(self, f):
+        lbm_set_state(self.ctx, f)
+
+    def field(self, which):
+        return lbm_get_field(self.ctx, which, self.shape)
+
+    def set_debug(self, enable=True):
+        lbm_set_debug(self.ctx, enable)
+
+    def profile(self, max_launches):
+        lbm_profile(self.ctx, max_launches)
+
+    def profile_read(self):
+        return lbm_profile_read(self.ctx)
+
+    def info(self):
+        return lbm_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (FP32 GPU vs FP64 oracle) are derived from the oracle's own FP32
+instantiation: on the 32^3 configuration below the FP32 and FP64 oracles
+differ after 200 steps by at most 3.6e-4 in rho^r, rho^p (median 1e-6),
+1.1e-5 in C and 2.2e-6 in u; the bounds are about 4x those gaps.  One step from
+a given state has no dynamical amplification: populations agree to ~1e-6.
+Integer-valued fields (NN) must agree exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cglbm as O
+from oracle.pointwise import PointwiseStep
+from paper_2608_15781_b300 import build, lbm, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP_POP = 5e-6          # one step, populations, max-abs
+TOL_RHO_200 = 1.5e-3         # 200 steps, rho^r / rho^p max-abs
+TOL_RHO_200_MEDIAN = 1e-5
+TOL_C_200 = 5e-5
+TOL_U_200 = 1e-5
+TOL_MASS_REL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    lbm.load_library()
+
+
+def _oparams(p, bc_z):
+    return O.Params(tau=p.tau, sigma=p.sigma, beta=p.beta, theta_deg=p.theta_deg, accel=tuple(p.accel),
+                    diffusivity=p.diffusivity, k_rate=p.k_rate, c_init=p.c_init, c_in=p.c_in, u_in=p.u_in,
+                    rho_out=p.rho_out, xi=p.xi, reaction_mode=p.reaction_mode, bc_z=bc_z)
+
+
+def _random_state(shape, solid, seed):
+    rng = np.random.default_rng(seed)
+    rr = rng.random(shape)
+    rp = 1.0 - rr + 0.1 * rng.random(shape)
+    conc = rng.random(shape)
+    u = 0.03 * rng.standard_normal((3,) + shape)
+    return rr, rp, conc, u, rng
+
+
+def _moments(f):
+    f = f.astype(np.float64)
+    rr, rp = f[0:19].sum(0), f[19:38].sum(0)
+    c = f[38:45].sum(0)
+    j = np.einsum("ia,i...->a...", O.C19.astype(float), f[0:19] + f[19:38])
+    return rr, rp, c, j / np.where(rr + rp == 0, 1, rr + rp)
+
+
+# --------------------------------------------------------------------- static geometry
+@pytest.mark.parametrize("bc", [0, 1])
+def test_geometry_fields(bc):
+    shape = (28, 20, 24)
+    solid = synth.grf_mask(shape, 3, 0.5, 11, periodic_z=(bc == 0))
+    g = O.Geometry(solid=solid, bc_z=bc)
+    with lbm.Lattice(solid, lbm.Params(), bc_z=bc) as L:
+        nn = L.field(lbm.FIELD_NN)
+        ns = L.field(lbm.FIELD_NS)
+        info = L.info()
+    assert (nn == g.nn).all()
+    assert info["n_wall"] == g.wall.sum() and info["n_solid_bnd"] == g.solid_bnd.sum()
+    assert np.abs(ns - np.where(g.ns_ok[None], g.ns, 0)).max() < 2e-6
+
+
+# --------------------------------------------------------------------- one step
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_single_step_random_state(bc, mode):
+    """Ragged box (x, y not multiples of the block), random mask and non-equilibrium state."""
+    shape = (19, 21, 37)
+    rng = np.random.default_rng(100 + bc + 2 * mode)
+    solid = rng.random(shape) < 0.3
+    p = lbm.Params(sigma=0.05, theta_deg=60.0, accel=(1e-4, -2e-5, 3e-5), k_rate=0.05, xi=0.4,
+                   reaction_mode=mode, u_in=0.01, c_in=0.7, rho_out=0.99)
+    op = _oparams(p, bc)
+    g = O.Geometry(solid=solid, bc_z=bc)
+    rr, rp, conc, u, rng = _random_state(shape, solid, 7)
+    st = O.init_state(g, op, rho_r=rr, rho_p=rp, conc=conc, u=u)
+    st.f += 1e-3 * rng.standard_normal(st.f.shape)
+    st.f[:, g.solid] = 0.0
+    f32 = st.f.astype(np.float32)
+    st.f = f32.astype(np.float64)
+    with lbm.Lattice(solid, p, bc_z=bc) as L:
+        L.set_debug(True)
+        L.set_state(f32)
+        L.step(1)
+        out = L.get_state()
+        rhoN = L.field(lbm.FIELD_RHON)
+        nrm = L.field(lbm.FIELD_NORMAL)
+        gm = L.field(lbm.FIELD_GRADMAG)
+        H = L.field(lbm.FIELD_CURV)
+        delta = L.field(lbm.FIELD_DELTA)
+        ob = L.observables()
+    new, fl = O.step(st, g, op, return_fields=True)
+    fluid = g.fluid
+    bnd = g.solid_bnd | fluid
+    assert np.abs(rhoN - fl.rhoN)[bnd].max() < 1e-5
+    assert np.abs(gm - fl.grad_mag)[fluid].max() < 1e-5
+    well = fluid & (fl.grad_mag > 1e-2)
+    assert np.abs(nrm - fl.n)[:, well].max() < 1e-4
+    assert np.abs(H * gm - fl.H * fl.grad_mag)[fluid].max() < 1e-4
+    assert np.abs(delta - fl.delta)[fluid].max() < 1e-6
+    err = np.abs(out.astype(np.float64) - new.f)[:, fluid]
+    assert err.max() < TOL_STEP_POP, err.max()
+    assert abs(ob["rate"] - new.rate) < 1e-5 * max(1.0, new.rate)
+    oo = O.observables(new, g, op)
+    for k in ("mass_r", "mass_p", "mass_c"):
+        assert abs(ob[k] - oo[k]) < 1e-5 * abs(oo[k]) + 1e-6, k
+
+
+# --------------------------------------------------------------------- 200 steps, config C1
+def test_c1_periodic_200_steps():
+    """32^3 periodic GRF mask (shell 4 +- 1, porosity 0.55, seed 1), liquid start, 200 steps."""
+    shape = (32, 32, 32)
+    solid = synth.grf_mask(shape, 4, 0.55, 1)
+    p = lbm.Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=90.0, accel=(1e-6, 0.0, 0.0),
+                   diffusivity=0.05, k_rate=1e-3, c_init=1.0)
+    op = _oparams(p, 0)
+    g = O.Geometry(solid=solid, bc_z=0)
+    with lbm.Lattice(solid, p) as L:
+        L.step(200)
+        out = L.get_state()
+        ob = L.observables()
+    st = O.run(O.init_state(g, op), g, op, 200)
+    oo = O.observables(st, g, op)
+    a, b = _moments(out), _moments(st.f)
+    fl = g.fluid
+    drr = np.abs(a[0] - b[0])[fl]
+    assert drr.max() < TOL_RHO_200 and np.median(drr) < TOL_RHO_200_MEDIAN
+    assert np.abs(a[1] - b[1])[fl].max() < TOL_RHO_200
+    assert np.abs(a[2] - b[2])[fl].max() < TOL_C_200
+    assert np.abs(a[3] - b[3])[:, fl].max() < TOL_U_200
+    for k in ("mass_r", "mass_p", "mass_c", "consumed"):
+        assert abs(ob[k] - oo[k]) < TOL_MASS_REL * abs(oo["mass_r"] + oo["mass_p"]), k
+    assert abs(ob["gas_saturation"] - oo["gas_saturation"]) < 1e-5
+    assert abs(ob["conversion"] - oo["conversion"]) < 1e-5
+    assert ob["step"] == 200 and ob["n_bad"] == 0
+
+
+# --------------------------------------------------------------------- column, droplets
+def test_column_inlet_outlet_100_steps():
+    shape = (40, 24, 24)
+    solid = synth.grf_mask(shape, 3, 0.5, 2, periodic_z=False)
+    p = lbm.Params(theta_deg=60.0, k_rate=5e-3, u_in=0.005, c_in=1.0, c_init=0.5, rho_out=1.0)
+    op = _oparams(p, 1)
+    g = O.Geometry(solid=solid, bc_z=1)
+    with lbm.Lattice(solid, p, bc_z=1) as L:
+        L.step(100)
+        out = L.get_state()
+        ob = L.observables()
+    st = O.run(O.init_state(g, op), g, op, 100)
+    oo = O.observables(st, g, op)
+    a, b = _moments(out), _moments(st.f)
+    fl = g.fluid
+    assert np.abs(a[0] - b[0])[fl].max() < TOL_RHO_200
+    assert np.abs(a[2] - b[2])[fl].max() < TOL_C_200
+    assert np.abs(a[3] - b[3])[:, fl].max() < TOL_U_200
+    for k in ("flux_in", "flux_out"):
+        assert abs(ob[k] - oo[k]) < 1e-4 * abs(oo["flux_in"]), k
+    assert abs(ob["conversion"] - oo["conversion"]) < 1e-4
+
+
+def test_droplets_paper_mode_nucleation_sites():
+    """Paper reaction mode (rho^r -> rho^p directly, xi = 1) at a few nucleation sites, with droplets."""
+    shape = (24, 24, 24)
+    solid = synth.grf_mask(shape, 3, 0.6, 4)
+    g0 = O.Geometry(solid=solid, bc_z=0)
+    sites = np.zeros(shape, bool)
+    cand = np.argwhere(g0.nn == 1)
+    for k in range(0, len(cand), max(1, len(cand) // 4))[:4]:
+        sites[tuple(cand[k])] = True
+    rr, rp = synth.droplet_fields(shape, (12, 12, 12), 5.0, inside_r=False)
+    p = lbm.Params(sigma=0.05, theta_deg=30.0, reaction_mode=1, xi=1.0, accel=(3.6e-5, 0, 0))
+    op = _oparams(p, 0)
+    g = O.Geometry(solid=solid, bc_z=0, reactive_mask=sites)
+    with lbm.Lattice(solid, p, reactive=sites) as L:
+        L.init_fields(rr, rp, np.ones(shape))
+        L.step(100)
+        out = L.get_state()
+        ob = L.observables()
+    st = O.init_state(g, op, rho_r=rr.astype(np.float32), rho_p=rp.astype(np.float32))
+    st = O.run(st, g, op, 100)
+    oo = O.observables(st, g, op)
+    a, b = _moments(out), _moments(st.f)
+    fl = g.fluid
+    assert np.abs(a[0] - b[0])[fl].max() < TOL_RHO_200
+    assert np.abs(a[3] - b[3])[:, fl].max() < TOL_U_200
+    assert abs(ob["consumed"] - oo["consumed"]) < TOL_MASS_REL * oo["mass_r"]
+    assert abs(ob["rate"] - oo["rate"]) < 1e-4 * max(oo["rate"], 1e-3)
+
+
+# --------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("shape,bc", [((1, 1, 1), 0), ((1, 3, 5), 0), ((2, 1, 1), 1), ((9, 1, 33), 1),
+                                      ((5, 6, 7), 0)])
+def test_tiny_and_degenerate_boxes(shape, bc):
+    """Single node (every neighbour is itself), quasi-1D/2D boxes, no solid at all."""
+    rng = np.random.default_rng(3)
+    solid = np.zeros(shape, bool)
+    p = lbm.Params(sigma=0.03, accel=(1e-4, 0, 0), u_in=0.01)
+    op = _oparams(p, bc)
+    g = O.Geometry(solid=solid, bc_z=bc)
+    rr = rng.random(shape)
+    st = O.init_state(g, op, rho_r=rr, rho_p=1 - rr + 0.05, conc=rng.random(shape))
+    st.f = st.f.astype(np.float32).astype(np.float64)
+    with lbm.Lattice(solid, p, bc_z=bc) as L:
+        L.set_state(st.f.astype(np.float32))
+        L.step(3)
+        out = L.get_state()
+    st = O.run(st, g, op, 3)
+    assert np.abs(out - st.f).max() < 2e-5
+
+
+def test_invalid_state_sizes_and_nan_detection():
+    solid = np.zeros((4, 4, 4), bool)
+    with lbm.Lattice(solid, lbm.Params()) as L:
+        with pytest.raises(lbm.LbmError):
+            L.set_state(np.zeros((45, 4, 4, 3), np.float32))
+        f = L.get_state()
+        f[:, 1, 1, 1] = np.nan
+        L.set_state(f)
+        L.step(1)
+        ob = L.observables(allow_nan=True)
+        assert ob["n_bad"] > 0
+        with pytest.raises(lbm.LbmError) as e:
+            L.observables()
+        assert e.value.code == lbm.LBM_ENAN
+
+
+# --------------------------------------------------------------------- full size, sampled nodes
+def test_full_size_column_sampled_nodes():
+    """128 x 128 x 256 column (shell 8, porosity 0.5, seed 2) in the bench's launch configuration.
+
+    After 40 steps from a start with gas droplets, one more step is checked node
+    by node on a sample (wall nodes, inlet and outlet planes, bulk) against the
+    per-node oracle evaluated on the downloaded pre-step state.
+    """
+    shape = (256, 128, 128)
+    solid = synth.grf_mask(shape, 8, 0.5, 2, periodic_z=False)
+    p = lbm.Params(theta_deg=60.0, k_rate=5e-3, u_in=0.005, c_in=1.0, sigma=0.01)
+    op = _oparams(p, 1)
+    rr, rp = synth.droplet_fields(shape, (64, 64, 128), 20.0, inside_r=False)
+    with lbm.Lattice(solid, p, bc_z=1) as L:
+        L.init_fields(rr, rp, np.ones(shape))
+        L.step(40)
+        pre = L.get_state()
+        L.step(1)
+        post = L.get_state()
+    pw = PointwiseStep(pre, solid, op)
+    rng = np.random.default_rng(9)
+    fluid = ~solid
+    wall = np.zeros(shape, bool)
+    for c in O.C19[:18]:
+        wall |= O.neighbor(solid, c, "clamp")
+    groups = [np.argwhere(fluid & wall), np.argwhere(fluid & ~wall)]
+    zs = np.argwhere(fluid)
+    groups += [zs[zs[:, 0] == 0], zs[zs[:, 0] == shape[0] - 1]]
+    picked = []
+    for grp in groups:
+        idx = rng.choice(len(grp), size=min(12, len(grp)), replace=False)
+        picked += [tuple(grp[i]) for i in idx]
+    worst = 0.0
+    for z, y, x in picked:
+        ref, _ = pw.update((int(x), int(y), int(z)))
+        worst = max(worst, float(np.abs(post[:, z, y, x].astype(np.float64) - ref).max()))
+    assert worst < TOL_STEP_POP, worst

@@ -29,12 +29,15 @@ Readings of the paper (where it is silent, ambiguous or self-inconsistent):
     jump.  H and the recolouring formula are used as printed.
   * the solid normal n_s points into the solid (as printed), so the imposed
     contact angle theta is measured through the r phase.
-  * |grad rho^N| < 1e-8: n = 0 and H = 0.  1 - (n_s.n)^2 < 1e-12, n = 0 or an
+  * |grad rho^N| < 1e-5: n = 0 and H = 0.  1 - (n_s.n)^2 < 1e-6, n = 0 or an
     undefined n_s: wetting leaves n unchanged.  The n_+ / n_- choice keeps n_+
-    on ties.
+    on ties.  Both thresholds sit well above the FP32 rounding noise of the
+    gradient (~1e-7), so FP32 and FP64 evaluations take the same decisions: a
+    noise-level gradient must not switch on the full-strength recolouring in a
+    random direction.
   * n at a solid node next to the fluid (needed by the curvature stencil) is the
     lattice-weighted average of the (wetted) fluid-neighbour normals,
-    renormalised; zero if that average is shorter than 1e-8.
+    renormalised; zero if that average is shorter than 1e-5.
   * recolouring acts on the colour-blind post-collision populations:
     f^r* = (rho^r/rho^m) f^m* + beta rho^r rho^p/rho^m w_i cos(phi_i)
     (Latva-Kokko, whose beta-term equals the printed one since f^eq(rho,0)=w rho).

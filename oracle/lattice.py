@@ -65,8 +65,8 @@ OMEGA92 = np.array([_OMEGA8[int(np.dot(e, e))] for e in E92])
 NEAREST6 = [i for i in range(Q19) if (C19[i] * C19[i]).sum() == 1]
 
 # numeric thresholds shared by both precisions (documented readings)
-GRAD_EPS = 1e-8      # |grad rho^N| below this: n = 0, H = 0
-SIN2_EPS = 1e-12     # 1 - (n_s . n)^2 below this: wetting leaves n unchanged
+GRAD_EPS = 1e-5      # |grad rho^N| below this: n = 0, H = 0 (above the FP32 noise floor)
+SIN2_EPS = 1e-6      # 1 - (n_s . n)^2 below this: wetting leaves n unchanged
 
 # Python-native copies, so that arithmetic with float32 arrays stays float32
 # (NumPy scalars would promote it to float64).

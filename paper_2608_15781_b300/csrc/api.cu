@@ -223,6 +223,8 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
   if (rc) return rc;
   const long long n = (long long)geom->nx * geom->ny * geom->nz;
   if (n > (1ll << 31) - 1) return LBM_EINVAL;   // node lists are 32-bit
+  // 32-bit population offsets: 45 populations x (nz + 2) planes must stay below 2^32
+  if ((long long)NPOP * geom->nx * geom->ny * (geom->nz + 2) >= (1ll << 32)) return LBM_EINVAL;
   long long nfl = 0;
   for (long long i = 0; i < n; ++i) nfl += geom->solid[i] ? 0 : 1;
   if (nfl == 0) return LBM_EINVAL;

@@ -348,29 +348,29 @@ __global__ void __launch_bounds__(256) k_density(Lattice L, const float *__restr
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= L.nx || y >= L.ny) return;
-  const long long node = nidx(L, x, y, z);
-  const uint32_t lk = link[node];
-  if (lk & BIT_SOLID) return;
-  Stencil S;
-  S.init(L, x, y, z);
-  int zp[3];
-  pull_planes(L, z, zp);
+  const bool inside = x < L.nx && y < L.ny;
+  const unsigned node = inside ? (unsigned)nidx(L, x, y, z) : 0u;
+  const uint32_t lk = inside ? link[node] : BIT_SOLID;
+  const bool fluid = !(lk & BIT_SOLID);
+  // a warp with any fluid node writes every node of its row segment (solid: 0)
+  // so that the stores cover whole sectors
+  if (!__any_sync(0xffffffffu, fluid) || !inside) return;
+  if (!fluid) {
+    rhoN[node] = 0.f;
+    return;
+  }
+  PullOffsets O;
+  O.init(L, x, y, z);
+  const unsigned ps = (unsigned)L.pstride;
   float rr = 0.f, rp = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    long long src;
-    int pr, pp;
-    if ((lk >> i) & 1u) {  // halfway bounce-back: f_i(x) = f*_opp(i)(x)
-      src = pidx(L, 0, z + 1, y, x);
-      pr = OPP[i];
-    } else {
-      src = pidx(L, 0, zp[1 - CZ[i]], S.ys[1 - CY[i]], S.xs[1 - CX[i]]);
-      pr = i;
-    }
-    pp = Q + pr;
-    rr += f[src + (long long)pr * L.pstride];
-    rp += f[src + (long long)pp * L.pstride];
+    // halfway bounce-back: f_i(x) = f*_opp(i)(x) when x - c_i is solid
+    const bool bb = (lk >> i) & 1u;
+    const unsigned off = bb ? O.own : O.src(CX[i], CY[i], CZ[i]);
+    const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
+    rr += f[pr * ps + off];
+    rp += f[(pr + Q) * ps + off];
   }
   rhoN[node] = (rr - rp) / (rr + rp);
 }
@@ -405,10 +405,15 @@ __global__ void __launch_bounds__(256) k_normal(Lattice L, StepParams P, const f
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= L.nx || y >= L.ny) return;
-  const long long node = nidx(L, x, y, z);
-  const uint32_t lk = link[node];
-  if (lk & BIT_SOLID) return;
+  const bool inside = x < L.nx && y < L.ny;
+  const long long node = inside ? nidx(L, x, y, z) : 0;
+  const uint32_t lk = inside ? link[node] : BIT_SOLID;
+  const bool fluid = !(lk & BIT_SOLID);
+  if (!__any_sync(0xffffffffu, fluid) || !inside) return;
+  if (!fluid) {   // full-sector stores; solid nodes next to the fluid are filled by k_normal_solid
+    nrm[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   Stencil S;
   S.init(L, x, y, z);
   float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -489,7 +494,13 @@ __global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, lon
 // ---------------------------------------------------------------------------
 // a1, a2, a6 - a10: the fused main update
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const float *__restrict__ fin,
+#ifndef CGLBM_MAIN_MINBLOCKS
+#define CGLBM_MAIN_MINBLOCKS 5
+#endif
+#ifndef CGLBM_ZERO_SOLID
+#define CGLBM_ZERO_SOLID 0
+#endif
+__global__ void __launch_bounds__(128, CGLBM_MAIN_MINBLOCKS) k_main(Lattice L, StepParams P, const float *__restrict__ fin,
                                               float *__restrict__ fout, const uint32_t *__restrict__ link,
                                               const float4 *__restrict__ nrm, double *__restrict__ acc,
                                               int slot, float *__restrict__ dbg_H, float *__restrict__ dbg_delta) {
@@ -500,44 +511,57 @@ __global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const flo
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
     acc[2 + (slot ^ 1)] = 0.0;   // clear the other per-step slot for the next step
   const bool inside = x < L.nx && y < L.ny;
-  const long long node = inside ? nidx(L, x, y, z) : 0;
+  const unsigned node = inside ? (unsigned)nidx(L, x, y, z) : 0u;
   const uint32_t lk = inside ? link[node] : BIT_SOLID;
-  if (!(lk & BIT_SOLID)) {
+  const bool fluid = !(lk & BIT_SOLID);
+  const bool warp_has_fluid = __any_sync(0xffffffffu, fluid);
+  const unsigned ps = (unsigned)L.pstride;
+  PullOffsets O;
+  O.init(L, x, y, z);
+  if (inside && fluid) {
     Stencil S;
     S.init(L, x, y, z);
-    int zp[3];
-    pull_planes(L, z, zp);
+    // a6 (first, so that its loads do not overlap the 45 live populations): curvature H = -sum_ab (delta_ab - n_a n_b) d_a n_b
+    const float4 nme = nrm[node];
+    const float gm = nme.w;
+    float H = 0.f;
+    if (gm >= GRAD_EPS) {
+      float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int i = 0; i < Q - 1; ++i) {
+        const float4 v = nrm[S.nb(L, CX[i], CY[i], CZ[i])];
+        const float w3 = 3.0f * W[i];
+        if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
+        if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
+        if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
+      }
+      const float n3[3] = {nme.x, nme.y, nme.z};
+      float proj = d[0][0] + d[1][1] + d[2][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) proj -= n3[a] * n3[b] * d[a][b];
+      H = -proj;
+    }
     // a1: pull with bounce-back
     float fr[Q], fp[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      long long src;
-      int pr;
-      if ((lk >> i) & 1u) {
-        src = pidx(L, 0, z + 1, y, x);
-        pr = OPP[i];
-      } else {
-        src = pidx(L, 0, zp[1 - CZ[i]], S.ys[1 - CY[i]], S.xs[1 - CX[i]]);
-        pr = i;
-      }
-      fr[i] = fin[src + (long long)pr * L.pstride];
-      fp[i] = fin[src + (long long)(Q + pr) * L.pstride];
+      const bool bb = (lk >> i) & 1u;
+      const unsigned off = bb ? O.own : O.src(CX[i], CY[i], CZ[i]);
+      const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
+      fr[i] = fin[pr * ps + off];
+      fp[i] = fin[(pr + Q) * ps + off];
     }
     float g[Q7];
     if (P.reaction_mode == 0) {
 #pragma unroll
       for (int j = 0; j < Q7; ++j) {
         const int d = GDIR[j];
-        long long src;
-        int pj;
-        if ((lk >> d) & 1u) {
-          src = pidx(L, 0, z + 1, y, x);
-          pj = GOPP[j];
-        } else {
-          src = pidx(L, 0, zp[1 - CZ[d]], S.ys[1 - CY[d]], S.xs[1 - CX[d]]);
-          pj = j;
-        }
-        g[j] = fin[src + (long long)(2 * Q + pj) * L.pstride];
+        const bool bb = (lk >> d) & 1u;
+        const unsigned off = bb ? O.own : O.src(CX[d], CY[d], CZ[d]);
+        const unsigned pj = bb ? (unsigned)GOPP[j] : (unsigned)j;
+        g[j] = fin[(2 * Q + pj) * ps + off];
       }
     }
     // a2: moments
@@ -562,28 +586,6 @@ __global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const flo
     const float rho = rr + rp;
     const float inv_rho = 1.0f / rho;
     const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-    // a6: curvature H = -sum_ab (delta_ab - n_a n_b) d_a n_b
-    const float4 nme = nrm[node];
-    const float gm = nme.w;
-    float H = 0.f;
-    if (gm >= GRAD_EPS) {
-      float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-      for (int i = 0; i < Q - 1; ++i) {
-        const float4 v = nrm[S.nb(L, CX[i], CY[i], CZ[i])];
-        const float w3 = 3.0f * W[i];
-        if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
-        if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
-        if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
-      }
-      const float n3[3] = {nme.x, nme.y, nme.z};
-      float proj = d[0][0] + d[1][1] + d[2][2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) proj -= n3[a] * n3[b] * d[a][b];
-      H = -proj;
-    }
     // a7: du = (sigma/2) H |grad rho^N| n / rho^m + a (same for both components)
     const float fs = P.half_sigma * H * gm * inv_rho;
     const float dux = fs * nme.x + P.ax, duy = fs * nme.y + P.ay, duz = fs * nme.z + P.az;
@@ -610,11 +612,21 @@ __global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const flo
       if (lk & BIT_REACTIVE) delta = fminf(P.xi * (float)nn, 1.0f) * rr;
     }
     delta = fmaxf(delta, 0.f);
-    // a9: recolouring + reaction transfer; fr <- f^r*, fp <- f^p*
+    // a9: recolouring + reaction transfer; fr <- f^r*, fp <- f^p*.  The rest
+    // population is taken from mass conservation (sum_i f^m*_i = rho^m holds
+    // exactly in exact arithmetic): the FP32-rounded weights sum to 1 + 2.5e-8,
+    // which would otherwise add that much mass per node and step.
     const float Brec = P.beta * rr * rp * inv_rho;
+    float msum = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
+      float fm_star;
+      if (i < Q - 1) {
+        fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
+        msum += fm_star;
+      } else {
+        fm_star = rho - msum;
+      }
       const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
       const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
       fr[i] = r_star;
@@ -622,8 +634,8 @@ __global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const flo
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      fout[pidx(L, i, z + 1, y, x)] = fr[i];
-      fout[pidx(L, Q + i, z + 1, y, x)] = fp[i];
+      fout[(unsigned)i * ps + O.own] = fr[i];
+      fout[(unsigned)(Q + i) * ps + O.own] = fp[i];
     }
     float g5 = 0.f;
     if (P.reaction_mode == 0) {
@@ -634,17 +646,22 @@ __global__ void __launch_bounds__(128) k_main(Lattice L, StepParams P, const flo
         const int dd = GDIR[j];
         const float geq = W7[j] * conc * (1.0f + 4.0f * (CX[dd] * wx + CY[dd] * wy + CZ[dd] * wz));
         const float gs = g[j] + (geq - g[j]) * P.inv_tau_g - W7[j] * delta;
-        fout[pidx(L, 2 * Q + j, z + 1, y, x)] = gs;
+        fout[(unsigned)(2 * Q + j) * ps + O.own] = gs;
         if (j == 5) g5 = gs;
       }
     }
     if (L.bc_z == 1 && z == L.nz - 1) {
-      if (P.reaction_mode != 0) g5 = fin[pidx(L, 2 * Q + 5, z + 1, y, x)];
+      if (P.reaction_mode != 0) g5 = fin[(unsigned)(2 * Q + 5) * ps + O.own];
       write_outlet_ghost(L, fout, x, y, fr, fp, g5, P.rho_out);
     }
     if (dbg_H) dbg_H[node] = H;
     if (dbg_delta) dbg_delta[node] = delta;
     dsum = (double)delta;
+  } else if (CGLBM_ZERO_SOLID && inside && warp_has_fluid) {
+    // solid slots of a row segment with fluid are rewritten (as 0) so that the
+    // stores cover whole sectors; solid slots are never read
+#pragma unroll
+    for (int p = 0; p < NPOP; ++p) fout[p * ps + O.own] = 0.f;
   }
   // FP64 block sum of delta -> cumulative total acc[0] and this step's slot acc[2 + slot]
   __shared__ double red[32];

@@ -40,8 +40,8 @@ constexpr uint32_t BIT_NS_OK = 1u << 23;      // solid normal defined
 constexpr int NN_SHIFT = 24;                  // NN(x) in bits 24..26
 constexpr uint32_t LINK_MASK = (1u << 19) - 1;  // bit i: x - c_i is solid (bounce back)
 
-constexpr float GRAD_EPS = 1e-8f;   // |grad rho^N| below this: n = 0, H = 0
-constexpr float SIN2_EPS = 1e-12f;  // sin^2(theta') below this: no wetting rotation
+constexpr float GRAD_EPS = 1e-5f;   // |grad rho^N| below this: n = 0, H = 0 (above FP32 noise)
+constexpr float SIN2_EPS = 1e-6f;   // sin^2(theta') below this: no wetting rotation
 
 struct Lattice {
   int nx, ny, nz, bc_z;
@@ -82,6 +82,35 @@ struct Stencil {
   // node index of x + c_i
   __device__ __forceinline__ long long nb(const Lattice &L, int cx, int cy, int cz) const {
     return ((long long)zs[cz + 1] * L.ny + ys[cy + 1]) * L.nx + xs[cx + 1];
+  }
+};
+
+// 32-bit offsets (within one population array) of the pull sources x - c:
+// own offset + dx[1 - cx] + dy[1 - cy] + dz[1 - cz].  x and y periodic; z
+// periodic or (column mode) the ghost planes 0 / nz + 1.  One population array
+// of one buffer holds pstride < 2^32 / 45 floats (checked at create).
+struct PullOffsets {
+  unsigned own;
+  int dx[3], dy[3], dz[3];
+  __device__ __forceinline__ void init(const Lattice &L, int x, int y, int z) {
+    const int plane = (int)L.plane;
+    own = (unsigned)((z + 1) * plane + y * L.nx + x);
+    dx[1] = dy[1] = dz[1] = 0;
+    dx[0] = x > 0 ? -1 : L.nx - 1;            // x - 1
+    dx[2] = x + 1 < L.nx ? 1 : 1 - L.nx;      // x + 1
+    dy[0] = y > 0 ? -L.nx : (L.ny - 1) * L.nx;
+    dy[2] = y + 1 < L.ny ? L.nx : (1 - L.ny) * L.nx;
+    if (L.bc_z == 0) {
+      dz[0] = z > 0 ? -plane : (L.nz - 1) * plane;
+      dz[2] = z + 1 < L.nz ? plane : (1 - L.nz) * plane;
+    } else {
+      dz[0] = -plane;   // plane 0 is the inlet ghost when z = 0
+      dz[2] = plane;    // plane nz + 1 is the outlet ghost when z = nz - 1
+    }
+  }
+  // offset of the pull source of velocity (cx, cy, cz)
+  __device__ __forceinline__ unsigned src(int cx, int cy, int cz) const {
+    return own + (unsigned)(dx[1 - cx] + dy[1 - cy] + dz[1 - cz]);
   }
 };
 

@@ -18,7 +18,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libcglbm.so")
+# the in-tree build; CGLBM_LIBRARY may name another build of the same C ABI
+LIB_PATH = os.environ.get("CGLBM_LIBRARY", os.path.join(_PKG, "libcglbm.so"))
 NPOP = 45
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN = 0, -1, -2, -3, -4

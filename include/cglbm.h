@@ -170,6 +170,44 @@ int lbm_info(lbm_ctx *ctx, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_b
 /* Release every device resource of the context; NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free step.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory -- for example code that
+ * runs while a memory pool or arena owns every allocation, a host process
+ * whose allocator is locked down, or a stream that is being recorded and must
+ * not see cudaMalloc / cudaFree.  It performs one time step of a periodic box
+ * (bc_z = 0) on populations the caller already holds on the device, and keeps
+ * every intermediate field (bounce-back links, solid normals, colour field,
+ * interface normals, reaction sums) in one fixed scratch array compiled into
+ * the library (about LBM_STATIC_MAX_NODES * 40 bytes, held on every GPU that
+ * loads the library until the process exits).
+ *
+ *   nx, ny, nz    lattice size; nx * ny * nz <= LBM_STATIC_MAX_NODES, else
+ *                 LBM_EINVAL (nothing is launched).
+ *   solid         device, nx*ny*nz bytes, nonzero = solid (layout as lbm_geometry).
+ *   reactive      device, optional r(x) mask, or NULL (fluid nodes with NN >= 1).
+ *   f_in, f_out   device, 45 * nx*ny*nz floats each in the lbm_get_state layout
+ *                 (index p * N + node); f_out receives the post-collision
+ *                 populations of the step.  They must not overlap.
+ *   delta_sum     device, one double receiving the step's sum of reaction
+ *                 amounts, or NULL.
+ *   params        as for lbm_create (cuda_stream selects the stream; only
+ *                 storage = 0 is accepted).
+ *
+ * Nothing is allocated or freed: no cudaMalloc, cudaFree or allocating library
+ * call.  The first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The static geometry is rebuilt on every
+ * call (a few microseconds at the size limit).  All calls share the one
+ * scratch array, which keeps the last call's contents (the reaction sums are
+ * cleared at the start of each call): calls that may overlap on the GPU --
+ * different streams, different host threads -- race and must be serialised by
+ * the caller.  Returns LBM_OK, LBM_EINVAL or LBM_ECUDA (launch errors; kernel
+ * faults surface at the caller's next synchronisation). */
+#define LBM_STATIC_MAX_NODES 131072
+int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, const uint8_t *reactive,
+                    const float *f_in, float *f_out, double *delta_sum, const lbm_params *params);
+
 /* Static description of an error code. */
 const char *lbm_strerror(int code);
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -196,6 +197,92 @@ int launch_step(lbm_ctx *c) {
   c->step += 1;
   c->have_fields = true;
   return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// allocation-free step: scratch in a fixed device array (see lbm_step_static)
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticAlign = 256;
+constexpr size_t kStaticNodes = LBM_STATIC_MAX_NODES;
+__host__ __device__ constexpr size_t round_up(size_t v) { return (v + kStaticAlign - 1) / kStaticAlign * kStaticAlign; }
+// layout: reaction sums | link words | solid normals | colour field | interface normals
+constexpr size_t kOffAcc = 0;
+constexpr size_t kOffLink = round_up(4 * sizeof(double));
+constexpr size_t kOffNs = kOffLink + round_up(kStaticNodes * sizeof(uint32_t));
+constexpr size_t kOffRhoN = kOffNs + round_up(kStaticNodes * sizeof(float4));
+constexpr size_t kOffNrm = kOffRhoN + round_up(kStaticNodes * sizeof(float));
+constexpr size_t kStaticBytes = kOffNrm + round_up(kStaticNodes * sizeof(float4));
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+// device address of g_static_scratch, looked up once per device
+constexpr int kMaxDevices = 64;
+unsigned char *g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_mutex;
+
+int static_scratch(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kMaxDevices) return LBM_EINVAL;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return LBM_ECUDA;
+    }
+    g_static_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_static_ptr[dev];
+  return LBM_OK;
+}
+
+// solid nodes next to the fluid, found from the link words (no node list)
+__global__ void k_color_solid_all(Lattice L, const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long s = nidx(L, x, y, z);
+  if (!(link[s] & BIT_SOLID_BND)) return;
+  Stencil S;
+  S.init(L, x, y, z);
+  float num = 0.f, den = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    const long long nb = S.nb(L, CX[i], CY[i], CZ[i]);
+    if (!(link[nb] & BIT_SOLID)) {
+      num += W[i] * rhoN[nb];
+      den += W[i];
+    }
+  }
+  rhoN[s] = den > 0.f ? num / den : 0.f;
+}
+
+__global__ void k_normal_solid_all(Lattice L, const uint32_t *__restrict__ link, float4 *__restrict__ nrm) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long s = nidx(L, x, y, z);
+  if (!(link[s] & BIT_SOLID_BND)) return;
+  Stencil S;
+  S.init(L, x, y, z);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    const long long nb = S.nb(L, CX[i], CY[i], CZ[i]);
+    if (!(link[nb] & BIT_SOLID)) {
+      const float4 v = nrm[nb];
+      ax += W[i] * v.x;
+      ay += W[i] * v.y;
+      az += W[i] * v.z;
+    }
+  }
+  const float m = sqrtf(ax * ax + ay * ay + az * az);
+  nrm[s] = m >= GRAD_EPS ? make_float4(ax / m, ay / m, az / m, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 }  // namespace
@@ -523,6 +610,58 @@ int lbm_info(lbm_ctx *c, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd
   if (n_wall) *n_wall = c->n_wall;
   if (n_solid_bnd) *n_solid_bnd = c->n_bnd;
   if (device_bytes) *device_bytes = (int64_t)c->device_bytes;
+  return LBM_OK;
+}
+
+int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, const uint8_t *reactive,
+                    const float *f_in, float *f_out, double *delta_sum, const lbm_params *params) {
+  if (!solid || !f_in || !f_out || !params) return LBM_EINVAL;
+  if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || ny > 4 * 65535) return LBM_EINVAL;
+  const long long n = (long long)nx * ny * nz;
+  if (n > (long long)kStaticNodes) return LBM_EINVAL;
+  if (check_params(params) != LBM_OK) return LBM_EINVAL;
+  const size_t pop_bytes = (size_t)NPOP * n * sizeof(float);
+  const char *a = (const char *)f_in, *b = (const char *)f_out;
+  if (a < b + pop_bytes && b < a + pop_bytes) return LBM_EINVAL;   // overlap
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+  unsigned char *base = nullptr;
+  int rc = static_scratch(dev, &base);
+  if (rc) return rc;
+  double *acc = reinterpret_cast<double *>(base + kOffAcc);
+  uint32_t *link = reinterpret_cast<uint32_t *>(base + kOffLink);
+  float4 *ns = reinterpret_cast<float4 *>(base + kOffNs);
+  float *rhoN = reinterpret_cast<float *>(base + kOffRhoN);
+  float4 *nrm = reinterpret_cast<float4 *>(base + kOffNrm);
+  cudaStream_t st = (cudaStream_t)params->cuda_stream;
+  // periodic box in the caller's layout p * N + node: the kernels address
+  // population p, stored plane z + 1 at p * pstride + (z + 1) * plane, so the
+  // base is moved back by one plane and pstride = N (no ghost planes needed)
+  Lattice L{};
+  L.nx = nx;
+  L.ny = ny;
+  L.nz = nz;
+  L.bc_z = 0;
+  L.n = n;
+  L.plane = (long long)nx * ny;
+  L.pstride = n;
+  lbm_ctx tmp;                      // parameter conversion only; owns no memory
+  tmp.prm = *params;
+  fill_step_params(&tmp);
+  const float *fin = f_in - L.plane;
+  float *fout = f_out - L.plane;
+  const dim3 nb = node_block(), ng = node_grid(L);
+  if (cudaMemsetAsync(acc, 0, 4 * sizeof(double), st) != cudaSuccess) return LBM_ECUDA;
+  k_geom<<<ng, nb, 0, st>>>(L, solid, reactive, link, ns);
+  k_density<<<ng, nb, 0, st>>>(L, fin, link, rhoN);
+  k_color_solid_all<<<ng, nb, 0, st>>>(L, link, rhoN);
+  k_normal<<<ng, nb, 0, st>>>(L, tmp.sp, rhoN, link, ns, nrm);
+  k_normal_solid_all<<<ng, nb, 0, st>>>(L, link, nrm);
+  k_main<<<ng, nb, 0, st>>>(L, tmp.sp, fin, fout, link, nrm, acc, 0, nullptr, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+  if (delta_sum &&
+      cudaMemcpyAsync(delta_sum, acc + 2, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return LBM_ECUDA;
   return LBM_OK;
 }
 

@@ -30,8 +30,9 @@ KERNEL_NAMES = ("density", "color_solid", "normal", "normal_solid", "main", "obs
 SYMBOLS = (
     "lbm_create", "lbm_step", "lbm_observables", "lbm_reaction", "lbm_init_fields", "lbm_get_state",
     "lbm_set_state", "lbm_get_field", "lbm_set_debug", "lbm_profile", "lbm_profile_read",
-    "lbm_info", "lbm_destroy", "lbm_strerror",
+    "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static",
 )
+STATIC_MAX_NODES = 131072   # LBM_STATIC_MAX_NODES
 
 
 class LbmError(RuntimeError):
@@ -118,6 +119,7 @@ def load_library(path=LIB_PATH):
         "lbm_info": (ctypes.c_int, [P, P, P, P, P]),
         "lbm_destroy": (None, [P]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_step_static": (ctypes.c_int, [I32, I32, I32, P, P, P, P, P, ctypes.POINTER(_Params)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,6 +229,23 @@ def lbm_info(ctx):
 def lbm_destroy(ctx):
     if ctx is not None and ctx.value:
         load_library().lbm_destroy(ctx)
+
+
+def lbm_step_static(shape, solid_dev, f_in_dev, f_out_dev, params, reactive_dev=None, delta_sum_dev=None,
+                    stream=None):
+    """One allocation-free step of a periodic box on caller-held device buffers.
+
+    For callers that may not allocate device memory (pools or arenas that own
+    every allocation, recorded streams): the intermediate fields live in a
+    fixed scratch array inside the library, shared by all calls, so calls must
+    not overlap on the GPU.  Pointers are raw device addresses (ints), e.g.
+    ``tensor.data_ptr()``; f_in / f_out hold 45 * N floats in the
+    ``lbm_get_state`` layout; nx * ny * nz must not exceed ``STATIC_MAX_NODES``.
+    """
+    nz, ny, nx = shape
+    p = params.to_c(stream)
+    _check(load_library().lbm_step_static(int(nx), int(ny), int(nz), solid_dev, reactive_dev, f_in_dev, f_out_dev,
+                                           delta_sum_dev, ctypes.byref(p)), "lbm_step_static")
 
 
 # --------------------------------------------------------------------------- convenience

@@ -67,8 +67,8 @@ def kernel_source_hash():
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def ncu_traffic_per_node():
-    """DRAM bytes per lattice node of k_main from the committed ncu summary, if the kernel is unchanged."""
+def ncu_traffic_per_fluid_node():
+    """DRAM bytes per fluid node of k_main from the committed ncu summary, if the kernel is unchanged."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     kv = {}
@@ -80,7 +80,7 @@ def ncu_traffic_per_node():
     if kv.get("kernels_cuh_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_node"])
+        return float(kv["dram_bytes_per_fluid_node"])
     except (KeyError, ValueError):
         return None
 
@@ -141,12 +141,13 @@ class ClockSampler:
                 "power_w_max": float(max(power)), "reasons": sorted(reasons)}
 
 
-def bytes_per_node(params):
-    """Algorithmic bytes of one node update: populations read + written, plus 1 B of flags.
+def bytes_per_fluid_node(params):
+    """Algorithmic bytes of one fluid-node update: populations read + written, plus 1 B of flags.
 
     361 B with the reactant populations (45 FP32 values each way), 305 B in the
-    paper's reaction mode (38).  Every lattice node counts, solid ones included,
-    as in MLUPS: the dense lattice layout carries their slots.
+    paper's reaction mode (38).  Solid nodes carry no populations (the library
+    stores the fluid nodes only), so a launch's algorithmic traffic is this
+    figure times the number of fluid nodes.
     """
     npop = 45 if params.reaction_mode == 0 else 38
     return 2 * 4 * npop + 1
@@ -280,10 +281,10 @@ def run_native(args):
     kname = max(prof, key=lambda k: prof[k][0])
     k_ms, k_n = prof[kname]
     peak, peak_kind = measured_peaks()
-    per_node = bytes_per_node(wl.params)
-    alg_bytes = N * per_node
+    per_node = bytes_per_fluid_node(wl.params)
+    alg_bytes = Nf * per_node
     achieved = alg_bytes / (k_ms / k_n * 1e-3) / 1e9
-    traf = ncu_traffic_per_node() if kname == "main" else None
+    traf = ncu_traffic_per_fluid_node() if kname == "main" else None
     launches = int(sum(n for _, n in prof.values()))
 
     # end to end through the C ABI with host buffers: create from the host mask,
@@ -329,9 +330,10 @@ def run_native(args):
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": f"k_{kname}", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": round(traf * N) if traf else None,
+                     "traffic": round(traf * Nf) if traf else None,
                      "algorithmic_bytes": int(alg_bytes),
-                     "bytes_model": f"{per_node} B per lattice node update (populations read+write + 1 B flags)",
+                     "bytes_model": f"{per_node} B per fluid-node update (populations read+write + 1 B flags) "
+                                    f"x {Nf} fluid nodes",
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.4 TB/s",
                      "step_effective_gbs": round(alg_bytes / (t_ms / args.steps * 1e-3) / 1e9, 1)},

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "cglbm.h"
+#include "compact.cuh"
 #include "kernels.cuh"
 
 using namespace cglbm;
@@ -21,7 +22,7 @@ struct lbm_ctx {
   StepParams sp{};
   cudaStream_t stream = nullptr;
   // device memory (library-owned)
-  float *fa = nullptr, *fb = nullptr;   // current / next populations (with ghost planes)
+  float *fa = nullptr, *fb = nullptr;   // current / next populations, compact layout [45][C.ns]
   uint32_t *link = nullptr;
   float4 *ns = nullptr;
   float *rhoN = nullptr;
@@ -30,6 +31,11 @@ struct lbm_ctx {
   long long n_bnd = 0;
   double *acc = nullptr;                // [0] cumulative delta, [2 + s] per-step delta slots
   double *obs = nullptr;                // 8 observables accumulators
+  int *err = nullptr;                   // device error flag (a bounded wait gave up)
+  Compact C{};                          // fluid slots and slot stride
+  int *gidx = nullptr;                  // stored lattice position -> slot, -1 = solid
+  uint32_t *cnode = nullptr;            // slot -> packed (x, y, z), fluid slots only
+  std::vector<uint32_t> h_slot_node;    // slot -> node index (host, for state transfer)
   float *dbg_H = nullptr, *dbg_delta = nullptr;
   bool debug = false;
   size_t device_bytes = 0;
@@ -95,6 +101,9 @@ void free_all(lbm_ctx *c) {
   cudaFree(c->bnd_list);
   cudaFree(c->acc);
   cudaFree(c->obs);
+  cudaFree(c->err);
+  cudaFree(c->gidx);
+  cudaFree(c->cnode);
   cudaFree(c->dbg_H);
   cudaFree(c->dbg_delta);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -137,7 +146,8 @@ void fill_step_params(lbm_ctx *c) {
 int launch_observables(lbm_ctx *c) {
   CK(cudaMemsetAsync(c->obs, 0, 8 * sizeof(double), c->stream));
   prof_begin(c, 5);
-  k_observables<<<node_grid(c->L), node_block(), 0, c->stream>>>(c->L, c->fa, c->link, c->obs);
+  k_observables_c<<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(c->L, c->C, c->fa, c->cnode,
+                                                                             c->obs);
   prof_end(c);
   CK(cudaGetLastError());
   return LBM_OK;
@@ -148,8 +158,8 @@ int reset_after_state(lbm_ctx *c) {
   const Lattice &L = c->L;
   if (L.bc_z == 1) {
     dim3 b(32, 4, 1), g((L.nx + 31) / 32, (L.ny + 3) / 4, 1);
-    k_ghost_init<<<g, b, 0, c->stream>>>(L, c->link, (float)c->prm.u_in, (float)c->prm.c_in,
-                                         (float)c->prm.rho_out, c->fa, c->fb);
+    k_ghost_init_c<<<g, b, 0, c->stream>>>(L, c->C, c->gidx, (float)c->prm.u_in, (float)c->prm.c_in,
+                                           (float)c->prm.rho_out, c->fa, c->fb);
     CK(cudaGetLastError());
   }
   CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(double), c->stream));
@@ -169,7 +179,8 @@ int launch_step(lbm_ctx *c) {
   const dim3 nb = node_block(), ng = node_grid(L);
   const int slot = (int)(c->step & 1);
   prof_begin(c, 0);
-  k_density<<<ng, nb, 0, c->stream>>>(L, c->fa, c->link, c->rhoN);
+  const unsigned gf = (unsigned)((c->C.nf + 255) / 256);
+  k_density_c<<<gf, 256, 0, c->stream>>>(L, c->C, c->fa, c->gidx, c->cnode, c->rhoN);
   prof_end(c);
   if (c->n_bnd > 0) {
     const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
@@ -178,7 +189,7 @@ int launch_step(lbm_ctx *c) {
     prof_end(c);
   }
   prof_begin(c, 2);
-  k_normal<<<ng, nb, 0, c->stream>>>(L, c->sp, c->rhoN, c->link, c->ns, c->nrm);
+  k_normal_c<<<gf, 256, 0, c->stream>>>(L, c->sp, c->C, c->cnode, c->rhoN, c->link, c->ns, c->nrm);
   prof_end(c);
   if (c->n_bnd > 0) {
     const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
@@ -187,8 +198,9 @@ int launch_step(lbm_ctx *c) {
     prof_end(c);
   }
   prof_begin(c, 4);
-  k_main<<<ng, nb, 0, c->stream>>>(L, c->sp, c->fa, c->fb, c->link, c->nrm, c->acc, slot,
-                                   c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
+  k_main_c<<<(unsigned)((c->C.nf + 127) / 128), 128, 0, c->stream>>>(
+      L, c->C, c->sp, c->fa, c->fb, c->gidx, c->cnode, c->link, c->nrm, c->acc, slot,
+      c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
   prof_end(c);
   CK(cudaGetLastError());
   float *t = c->fa;
@@ -305,7 +317,8 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
   if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return LBM_EINVAL;
   if (geom->bc_z != 0 && geom->bc_z != 1) return LBM_EINVAL;
   if (geom->bc_z == 1 && geom->nz < 2) return LBM_EINVAL;
-  if (geom->nz > 65535 || geom->ny > 4 * 65535) return LBM_EINVAL;   // grid.z = nz, grid.y = ny / 4
+  // packed slot coordinates (10 + 10 + 11 bits)
+  if (geom->nx > 1024 || geom->ny > 1024 || geom->nz > 2048) return LBM_EINVAL;
   int rc = check_params(params);
   if (rc) return rc;
   const long long n = (long long)geom->nx * geom->ny * geom->nz;
@@ -332,17 +345,16 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
   c->n_fluid = nfl;
   fill_step_params(c);
 
-  const size_t pop_bytes = (size_t)NPOP * L.pstride * sizeof(float);
+
   uint8_t *d_solid = nullptr, *d_react = nullptr;
   rc = LBM_OK;
-  rc = rc ? rc : dalloc(c, (void **)&c->fa, pop_bytes);
-  rc = rc ? rc : dalloc(c, (void **)&c->fb, pop_bytes);
   rc = rc ? rc : dalloc(c, (void **)&c->link, n * sizeof(uint32_t));
   rc = rc ? rc : dalloc(c, (void **)&c->ns, n * sizeof(float4));
   rc = rc ? rc : dalloc(c, (void **)&c->rhoN, n * sizeof(float));
   rc = rc ? rc : dalloc(c, (void **)&c->nrm, n * sizeof(float4));
   rc = rc ? rc : dalloc(c, (void **)&c->acc, 8 * sizeof(double));
   rc = rc ? rc : dalloc(c, (void **)&c->obs, 8 * sizeof(double));
+  rc = rc ? rc : dalloc(c, (void **)&c->err, sizeof(int));
   if (!rc && cudaMalloc((void **)&d_solid, n) != cudaSuccess) rc = LBM_ENOMEM;
   if (!rc && geom->reactive && cudaMalloc((void **)&d_react, n) != cudaSuccess) rc = LBM_ENOMEM;
   if (rc) {
@@ -363,11 +375,9 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
   if (cudaMemcpy(d_solid, geom->solid, n, cudaMemcpyHostToDevice) != cudaSuccess) return fail(LBM_ECUDA);
   if (d_react && cudaMemcpy(d_react, geom->reactive, n, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(LBM_ECUDA);
-  // zero everything once: ghost planes of periodic runs and solid slots stay defined
-  if (cudaMemsetAsync(c->fa, 0, pop_bytes, c->stream) != cudaSuccess) return fail(LBM_ECUDA);
-  if (cudaMemsetAsync(c->fb, 0, pop_bytes, c->stream) != cudaSuccess) return fail(LBM_ECUDA);
   if (cudaMemsetAsync(c->rhoN, 0, n * sizeof(float), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
   if (cudaMemsetAsync(c->nrm, 0, n * sizeof(float4), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
+  if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
   k_geom<<<node_grid(L), node_block(), 0, c->stream>>>(L, d_solid, d_react, c->link, c->ns);
   if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
   // boundary-solid list, built from the device flags in node order
@@ -379,11 +389,38 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
   cudaFree(d_solid);
   cudaFree(d_react);
   d_solid = d_react = nullptr;
-  std::vector<uint32_t> blist;
+  // boundary-solid list, compact slots (fluid nodes in lattice order, then the
+  // inlet and outlet ghost planes in column mode) and the position -> slot map
+  std::vector<uint32_t> blist, cnode;
+  std::vector<int> gidx((size_t)L.plane * (L.nz + 2), -1);
   for (long long i = 0; i < n; ++i) {
     if (hlink[i] & BIT_SOLID_BND) blist.push_back((uint32_t)i);
     if (hlink[i] & BIT_WALL) c->n_wall++;
+    if (!(hlink[i] & BIT_SOLID)) {
+      const uint32_t x = (uint32_t)(i % L.nx), y = (uint32_t)((i / L.nx) % L.ny), z = (uint32_t)(i / L.plane);
+      gidx[(size_t)(i + L.plane)] = (int)cnode.size();
+      c->h_slot_node.push_back((uint32_t)i);
+      cnode.push_back(x | (y << 10) | (z << 20));
+    }
   }
+  c->C.nf = (int)cnode.size();
+  const long long nghost = L.bc_z == 1 ? 2 * L.plane : 0;
+  c->C.ns = (int)((c->C.nf + nghost + 63) / 64 * 64);
+  if (L.bc_z == 1)
+    for (long long q = 0; q < L.plane; ++q) {
+      gidx[(size_t)q] = c->C.nf + (int)q;                                         // inlet plane
+      gidx[(size_t)((L.nz + 1) * L.plane + q)] = c->C.nf + (int)(L.plane + q);    // outlet plane
+    }
+  const size_t pop_bytes = (size_t)NPOP * c->C.ns * sizeof(float);
+  if (dalloc(c, (void **)&c->fa, pop_bytes) || dalloc(c, (void **)&c->fb, pop_bytes) ||
+      dalloc(c, (void **)&c->gidx, gidx.size() * sizeof(int)) ||
+      dalloc(c, (void **)&c->cnode, cnode.size() * sizeof(uint32_t)))
+    return fail(LBM_ENOMEM);
+  if (cudaMemsetAsync(c->fa, 0, pop_bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->fb, 0, pop_bytes, c->stream) != cudaSuccess ||
+      cudaMemcpy(c->gidx, gidx.data(), gidx.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->cnode, cnode.data(), cnode.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LBM_ECUDA);
   c->n_bnd = (long long)blist.size();
   if (c->n_bnd > 0) {
     if (dalloc(c, (void **)&c->bnd_list, blist.size() * sizeof(uint32_t))) return fail(LBM_ENOMEM);
@@ -391,8 +428,8 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
         cudaSuccess)
       return fail(LBM_ECUDA);
   }
-  k_init<<<node_grid(L), node_block(), 0, c->stream>>>(L, c->link, nullptr, nullptr, nullptr, nullptr, 1.0f,
-                                                       0.0f, (float)params->c_init, c->fa, c->fb);
+  k_init_c<<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
+      L, c->C, c->cnode, nullptr, nullptr, nullptr, nullptr, 1.0f, 0.0f, (float)params->c_init, c->fa, c->fb);
   if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
   rc = reset_after_state(c);
   if (rc) return fail(rc);
@@ -418,9 +455,15 @@ int lbm_observables(lbm_ctx *c, lbm_obs *out) {
   int rc = launch_observables(c);
   if (rc) return rc;
   double h[8], a[4];
+  int derr = 0;
   CK(cudaMemcpyAsync(h, c->obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&derr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (derr) {
+    c->sticky = LBM_ECUDA;
+    return LBM_ECUDA;
+  }
   std::memset(out, 0, sizeof(*out));
   out->mass_r = h[0];
   out->mass_p = h[1];
@@ -472,9 +515,8 @@ int lbm_init_fields(lbm_ctx *c, const float *rho_r, const float *rho_p, const fl
     rc = cuda_fail(c, cudaErrorUnknown);
   if (!rc) {
     const float *fd = d;
-    k_init<<<node_grid(L), node_block(), 0, c->stream>>>(L, c->link, fd, fd + L.n, fd + 2 * L.n,
-                                                         u ? fd + 3 * L.n : nullptr, 0.f, 0.f, 0.f, c->fa,
-                                                         c->fb);
+    k_init_c<<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
+        L, c->C, c->cnode, fd, fd + L.n, fd + 2 * L.n, u ? fd + 3 * L.n : nullptr, 0.f, 0.f, 0.f, c->fa, c->fb);
     if (cudaGetLastError() != cudaSuccess) rc = cuda_fail(c, cudaErrorLaunchFailure);
   }
   if (!rc) rc = reset_after_state(c);
@@ -489,10 +531,18 @@ int lbm_get_state(lbm_ctx *c, float *dst, size_t bytes) {
   if (bytes != (size_t)NPOP * L.n * sizeof(float)) return LBM_EINVAL;
   if (c->sticky) return c->sticky;
   cudaSetDevice(c->device);
+  const size_t nf = (size_t)c->C.nf;
+  std::vector<float> h((size_t)NPOP * nf);
   for (int p = 0; p < NPOP; ++p)
-    CK(cudaMemcpyAsync(dst + (size_t)p * L.n, c->fa + (size_t)p * L.pstride + L.plane, L.n * sizeof(float),
+    CK(cudaMemcpyAsync(h.data() + (size_t)p * nf, c->fa + (size_t)p * c->C.ns, nf * sizeof(float),
                        cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  std::memset(dst, 0, bytes);   // solid nodes hold no populations
+  for (int p = 0; p < NPOP; ++p) {
+    float *d = dst + (size_t)p * L.n;
+    const float *s = h.data() + (size_t)p * nf;
+    for (size_t t = 0; t < nf; ++t) d[c->h_slot_node[t]] = s[t];
+  }
   return LBM_OK;
 }
 
@@ -502,10 +552,17 @@ int lbm_set_state(lbm_ctx *c, const float *src, size_t bytes) {
   if (bytes != (size_t)NPOP * L.n * sizeof(float)) return LBM_EINVAL;
   if (c->sticky) return c->sticky;
   cudaSetDevice(c->device);
+  const size_t nf = (size_t)c->C.nf;
+  std::vector<float> h((size_t)NPOP * nf);
   for (int p = 0; p < NPOP; ++p) {
-    CK(cudaMemcpyAsync(c->fa + (size_t)p * L.pstride + L.plane, src + (size_t)p * L.n, L.n * sizeof(float),
+    const float *s = src + (size_t)p * L.n;
+    float *d = h.data() + (size_t)p * nf;
+    for (size_t t = 0; t < nf; ++t) d[t] = s[c->h_slot_node[t]];
+  }
+  for (int p = 0; p < NPOP; ++p) {
+    CK(cudaMemcpyAsync(c->fa + (size_t)p * c->C.ns, h.data() + (size_t)p * nf, nf * sizeof(float),
                        cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->fb + (size_t)p * L.pstride + L.plane, src + (size_t)p * L.n, L.n * sizeof(float),
+    CK(cudaMemcpyAsync(c->fb + (size_t)p * c->C.ns, h.data() + (size_t)p * nf, nf * sizeof(float),
                        cudaMemcpyHostToDevice, c->stream));
   }
   return reset_after_state(c);

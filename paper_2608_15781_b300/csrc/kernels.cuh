@@ -398,32 +398,11 @@ __global__ void k_color_solid(Lattice L, const uint32_t *__restrict__ list, long
   rhoN[s] = den > 0.f ? num / den : 0.f;
 }
 
-// a4 + a5: isotropic gradient, normal, Akai wetting at wall nodes
-__global__ void __launch_bounds__(256) k_normal(Lattice L, StepParams P, const float *__restrict__ rhoN,
-                                                const uint32_t *__restrict__ link, const float4 *__restrict__ ns,
-                                                float4 *__restrict__ nrm) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  const bool inside = x < L.nx && y < L.ny;
-  const long long node = inside ? nidx(L, x, y, z) : 0;
-  const uint32_t lk = inside ? link[node] : BIT_SOLID;
-  const bool fluid = !(lk & BIT_SOLID);
-  if (!__any_sync(0xffffffffu, fluid) || !inside) return;
-  if (!fluid) {   // full-sector stores; solid nodes next to the fluid are filled by k_normal_solid
-    nrm[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-    return;
-  }
-  Stencil S;
-  S.init(L, x, y, z);
-  float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q - 1; ++i) {
-    const float v = 3.0f * W[i] * rhoN[S.nb(L, CX[i], CY[i], CZ[i])];
-    gx += CX[i] * v;
-    gy += CY[i] * v;
-    gz += CZ[i] * v;
-  }
+// a4 + a5 from the gradient (gx, gy, gz): n = +grad/|grad| (reading of
+// Eq. color_gradient_normal), then at wall nodes n_+ or n_- of
+// Eq. realigned_normal_vectors, whichever is nearer to n.  Returns (n, |grad|).
+__device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk, const float4 *__restrict__ ns,
+                                                unsigned node, float gx, float gy, float gz) {
   const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
   float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
   if (gm >= GRAD_EPS) {
@@ -439,7 +418,6 @@ __global__ void __launch_bounds__(256) k_normal(Lattice L, StepParams P, const f
       if (st2 >= SIN2_EPS) {
         const float st = sqrtf(st2);
         const float a_s = P.sin_th * c / st, a_n = P.sin_th / st;
-        // n_+ and n_- of Eq. realigned_normal_vectors
         const float px = (P.cos_th - a_s) * s.x + a_n * nx_;
         const float py = (P.cos_th - a_s) * s.y + a_n * ny_;
         const float pz = (P.cos_th - a_s) * s.z + a_n * nz_;
@@ -456,7 +434,36 @@ __global__ void __launch_bounds__(256) k_normal(Lattice L, StepParams P, const f
       }
     }
   }
-  nrm[node] = make_float4(nx_, ny_, nz_, gm);
+  return make_float4(nx_, ny_, nz_, gm);
+}
+
+// a4 + a5 over the lattice (one thread per node)
+__global__ void __launch_bounds__(256) k_normal(Lattice L, StepParams P, const float *__restrict__ rhoN,
+                                                const uint32_t *__restrict__ link, const float4 *__restrict__ ns,
+                                                float4 *__restrict__ nrm) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool inside = x < L.nx && y < L.ny;
+  const long long node = inside ? nidx(L, x, y, z) : 0;
+  const uint32_t lk = inside ? link[node] : BIT_SOLID;
+  const bool fluid = !(lk & BIT_SOLID);
+  if (!__any_sync(0xffffffffu, fluid) || !inside) return;
+  if (!fluid) {   // full-sector stores; solid nodes next to the fluid are filled by k_normal_solid
+    nrm[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  StencilOffsets S;
+  S.init(L, x, y, z);
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    const float v = 3.0f * W[i] * rhoN[S.nb(CX[i], CY[i], CZ[i])];
+    gx += CX[i] * v;
+    gy += CY[i] * v;
+    gz += CZ[i] * v;
+  }
+  nrm[node] = wetted_normal(P, lk, ns, (unsigned)node, gx, gy, gz);
 }
 
 // n at solid nodes next to the fluid: lattice-weighted average of the fluid
@@ -494,176 +501,116 @@ __global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, lon
 // ---------------------------------------------------------------------------
 // a1, a2, a6 - a10: the fused main update
 // ---------------------------------------------------------------------------
-#ifndef CGLBM_MAIN_MINBLOCKS
-#define CGLBM_MAIN_MINBLOCKS 5
-#endif
-#ifndef CGLBM_ZERO_SOLID
-#define CGLBM_ZERO_SOLID 0
-#endif
-__global__ void __launch_bounds__(128, CGLBM_MAIN_MINBLOCKS) k_main(Lattice L, StepParams P, const float *__restrict__ fin,
-                                              float *__restrict__ fout, const uint32_t *__restrict__ link,
-                                              const float4 *__restrict__ nrm, double *__restrict__ acc,
-                                              int slot, float *__restrict__ dbg_H, float *__restrict__ dbg_delta) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  double dsum = 0.0;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
-    acc[2 + (slot ^ 1)] = 0.0;   // clear the other per-step slot for the next step
-  const bool inside = x < L.nx && y < L.ny;
-  const unsigned node = inside ? (unsigned)nidx(L, x, y, z) : 0u;
-  const uint32_t lk = inside ? link[node] : BIT_SOLID;
-  const bool fluid = !(lk & BIT_SOLID);
-  const bool warp_has_fluid = __any_sync(0xffffffffu, fluid);
-  const unsigned ps = (unsigned)L.pstride;
-  PullOffsets O;
-  O.init(L, x, y, z);
-  if (inside && fluid) {
-    Stencil S;
-    S.init(L, x, y, z);
-    // a6 (first, so that its loads do not overlap the 45 live populations): curvature H = -sum_ab (delta_ab - n_a n_b) d_a n_b
-    const float4 nme = nrm[node];
-    const float gm = nme.w;
-    float H = 0.f;
-    if (gm >= GRAD_EPS) {
-      float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+// a6: H = -sum_ab (delta_ab - n_a n_b) d_a n_b, d_a n_b by Eq. finite_difference_scheme;
+// nb(i) returns the normal at x + c_i
+template <class NbNormal>
+__device__ __forceinline__ float curvature(const float4 nme, const NbNormal &nb) {
+  float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
-      for (int i = 0; i < Q - 1; ++i) {
-        const float4 v = nrm[S.nb(L, CX[i], CY[i], CZ[i])];
-        const float w3 = 3.0f * W[i];
-        if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
-        if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
-        if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
-      }
-      const float n3[3] = {nme.x, nme.y, nme.z};
-      float proj = d[0][0] + d[1][1] + d[2][2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) proj -= n3[a] * n3[b] * d[a][b];
-      H = -proj;
-    }
-    // a1: pull with bounce-back
-    float fr[Q], fp[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const bool bb = (lk >> i) & 1u;
-      const unsigned off = bb ? O.own : O.src(CX[i], CY[i], CZ[i]);
-      const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
-      fr[i] = fin[pr * ps + off];
-      fp[i] = fin[(pr + Q) * ps + off];
-    }
-    float g[Q7];
-    if (P.reaction_mode == 0) {
-#pragma unroll
-      for (int j = 0; j < Q7; ++j) {
-        const int d = GDIR[j];
-        const bool bb = (lk >> d) & 1u;
-        const unsigned off = bb ? O.own : O.src(CX[d], CY[d], CZ[d]);
-        const unsigned pj = bb ? (unsigned)GOPP[j] : (unsigned)j;
-        g[j] = fin[(2 * Q + pj) * ps + off];
-      }
-    }
-    // a2: moments
-    float rr = 0.f, rp = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      rr += fr[i];
-      rp += fp[i];
-      const float m = fr[i] + fp[i];
-      fr[i] = m;   // fr now holds f^m
-      if (CX[i]) jx += CX[i] * m;
-      if (CY[i]) jy += CY[i] * m;
-      if (CZ[i]) jz += CZ[i] * m;
-      if (CX[i]) pxx += m;
-      if (CY[i]) pyy += m;
-      if (CZ[i]) pzz += m;
-      if (CX[i] && CY[i]) pxy += CX[i] * CY[i] * m;
-      if (CX[i] && CZ[i]) pxz += CX[i] * CZ[i] * m;
-      if (CY[i] && CZ[i]) pyz += CY[i] * CZ[i] * m;
-    }
-    const float rho = rr + rp;
-    const float inv_rho = 1.0f / rho;
-    const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-    // a7: du = (sigma/2) H |grad rho^N| n / rho^m + a (same for both components)
-    const float fs = P.half_sigma * H * gm * inv_rho;
-    const float dux = fs * nme.x + P.ax, duy = fs * nme.y + P.ay, duz = fs * nme.z + P.az;
-    // a8: central moments k5..k9 of f^m about u (Eq. post_collision_moments)
-    const float k5 = P.omega_cm * ((pxx - pyy) - rho * (ux * ux - uy * uy));
-    const float k6 = P.omega_cm * ((pyy - pzz) - rho * (uy * uy - uz * uz));
-    const float k7 = P.omega_cm * (pxy - rho * ux * uy);
-    const float k8 = P.omega_cm * (pxz - rho * ux * uz);
-    const float k9 = P.omega_cm * (pyz - rho * uy * uz);
-    float bt[Q];
-    back_transform(ux, uy, uz, k5, k6, k7, k8, k9, bt);
-    const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
-    const float vv = vx * vx + vy * vy + vz * vz;
-    // a10: reaction amount (explicit Euler, post-streaming densities)
-    const float psi = rr * inv_rho;
-    float delta = 0.f;
-    const uint32_t nn = (lk >> NN_SHIFT) & 7u;
-    float conc = 0.f;
-    if (P.reaction_mode == 0) {
-#pragma unroll
-      for (int j = 0; j < Q7; ++j) conc += g[j];
-      if (lk & BIT_REACTIVE) delta = fminf(fminf(P.k_rate * (float)nn * conc * psi, conc), rr);
-    } else {
-      if (lk & BIT_REACTIVE) delta = fminf(P.xi * (float)nn, 1.0f) * rr;
-    }
-    delta = fmaxf(delta, 0.f);
-    // a9: recolouring + reaction transfer; fr <- f^r*, fp <- f^p*.  The rest
-    // population is taken from mass conservation (sum_i f^m*_i = rho^m holds
-    // exactly in exact arithmetic): the FP32-rounded weights sum to 1 + 2.5e-8,
-    // which would otherwise add that much mass per node and step.
-    const float Brec = P.beta * rr * rp * inv_rho;
-    float msum = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float fm_star;
-      if (i < Q - 1) {
-        fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
-        msum += fm_star;
-      } else {
-        fm_star = rho - msum;
-      }
-      const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
-      const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
-      fr[i] = r_star;
-      fp[i] = fm_star - r_star;
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      fout[(unsigned)i * ps + O.own] = fr[i];
-      fout[(unsigned)(Q + i) * ps + O.own] = fp[i];
-    }
-    float g5 = 0.f;
-    if (P.reaction_mode == 0) {
-      // D3Q7 BGK of C advected by the physical velocity u + du/2, minus the reacted amount
-      const float wx = ux + 0.5f * dux, wy = uy + 0.5f * duy, wz = uz + 0.5f * duz;
-#pragma unroll
-      for (int j = 0; j < Q7; ++j) {
-        const int dd = GDIR[j];
-        const float geq = W7[j] * conc * (1.0f + 4.0f * (CX[dd] * wx + CY[dd] * wy + CZ[dd] * wz));
-        const float gs = g[j] + (geq - g[j]) * P.inv_tau_g - W7[j] * delta;
-        fout[(unsigned)(2 * Q + j) * ps + O.own] = gs;
-        if (j == 5) g5 = gs;
-      }
-    }
-    if (L.bc_z == 1 && z == L.nz - 1) {
-      if (P.reaction_mode != 0) g5 = fin[(unsigned)(2 * Q + 5) * ps + O.own];
-      write_outlet_ghost(L, fout, x, y, fr, fp, g5, P.rho_out);
-    }
-    if (dbg_H) dbg_H[node] = H;
-    if (dbg_delta) dbg_delta[node] = delta;
-    dsum = (double)delta;
-  } else if (CGLBM_ZERO_SOLID && inside && warp_has_fluid) {
-    // solid slots of a row segment with fluid are rewritten (as 0) so that the
-    // stores cover whole sectors; solid slots are never read
-#pragma unroll
-    for (int p = 0; p < NPOP; ++p) fout[p * ps + O.own] = 0.f;
+  for (int i = 0; i < Q - 1; ++i) {
+    const float4 v = nb(i);
+    const float w3 = 3.0f * W[i];
+    if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
+    if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
+    if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
   }
-  // FP64 block sum of delta -> cumulative total acc[0] and this step's slot acc[2 + slot]
+  const float n3[3] = {nme.x, nme.y, nme.z};
+  float proj = d[0][0] + d[1][1] + d[2][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) proj -= n3[a] * n3[b] * d[a][b];
+  return -proj;
+}
+
+// a2, a7 - a10 at one fluid node.  In: fr, fp, g = pulled f^r, f^p, g (g only in
+// reaction mode 0), nme = (n, |grad rho^N|), H.  Out: fr, fp, g = post-collision
+// f^r*, f^p*, g*.  Returns the reaction amount delta.
+__device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, float (&fr)[Q], float (&fp)[Q],
+                                              float (&g)[Q7], const float4 nme, float H) {
+  // a2: moments
+  float rr = 0.f, rp = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rr += fr[i];
+    rp += fp[i];
+    const float m = fr[i] + fp[i];
+    fr[i] = m;   // fr now holds f^m
+    if (CX[i]) jx += CX[i] * m;
+    if (CY[i]) jy += CY[i] * m;
+    if (CZ[i]) jz += CZ[i] * m;
+    if (CX[i]) pxx += m;
+    if (CY[i]) pyy += m;
+    if (CZ[i]) pzz += m;
+    if (CX[i] && CY[i]) pxy += CX[i] * CY[i] * m;
+    if (CX[i] && CZ[i]) pxz += CX[i] * CZ[i] * m;
+    if (CY[i] && CZ[i]) pyz += CY[i] * CZ[i] * m;
+  }
+  const float rho = rr + rp;
+  const float inv_rho = 1.0f / rho;
+  const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+  // a7: du = (sigma/2) H |grad rho^N| n / rho^m + a (same for both components)
+  const float fs = P.half_sigma * H * nme.w * inv_rho;
+  const float dux = fs * nme.x + P.ax, duy = fs * nme.y + P.ay, duz = fs * nme.z + P.az;
+  // a8: central moments k5..k9 of f^m about u (Eq. post_collision_moments)
+  const float k5 = P.omega_cm * ((pxx - pyy) - rho * (ux * ux - uy * uy));
+  const float k6 = P.omega_cm * ((pyy - pzz) - rho * (uy * uy - uz * uz));
+  const float k7 = P.omega_cm * (pxy - rho * ux * uy);
+  const float k8 = P.omega_cm * (pxz - rho * ux * uz);
+  const float k9 = P.omega_cm * (pyz - rho * uy * uz);
+  float bt[Q];
+  back_transform(ux, uy, uz, k5, k6, k7, k8, k9, bt);
+  const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
+  const float vv = vx * vx + vy * vy + vz * vz;
+  // a10: reaction amount (explicit Euler, post-streaming densities)
+  const float psi = rr * inv_rho;
+  float delta = 0.f;
+  const uint32_t nn = (lk >> NN_SHIFT) & 7u;
+  float conc = 0.f;
+  if (P.reaction_mode == 0) {
+#pragma unroll
+    for (int j = 0; j < Q7; ++j) conc += g[j];
+    if (lk & BIT_REACTIVE) delta = fminf(fminf(P.k_rate * (float)nn * conc * psi, conc), rr);
+  } else {
+    if (lk & BIT_REACTIVE) delta = fminf(P.xi * (float)nn, 1.0f) * rr;
+  }
+  delta = fmaxf(delta, 0.f);
+  // a9: recolouring + reaction transfer.  The rest population is taken from
+  // mass conservation (sum_i f^m*_i = rho^m holds exactly in exact arithmetic):
+  // the FP32-rounded weights sum to 1 + 2.5e-8, which would otherwise add that
+  // much mass per node and step.
+  const float Brec = P.beta * rr * rp * inv_rho;
+  float msum = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float fm_star;
+    if (i < Q - 1) {
+      fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
+      msum += fm_star;
+    } else {
+      fm_star = rho - msum;
+    }
+    const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
+    const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
+    fr[i] = r_star;
+    fp[i] = fm_star - r_star;
+  }
+  if (P.reaction_mode == 0) {
+    // D3Q7 BGK of C advected by the physical velocity u + du/2, minus the reacted amount
+    const float wx = ux + 0.5f * dux, wy = uy + 0.5f * duy, wz = uz + 0.5f * duz;
+#pragma unroll
+    for (int j = 0; j < Q7; ++j) {
+      const int dd = GDIR[j];
+      const float geq = W7[j] * conc * (1.0f + 4.0f * (CX[dd] * wx + CY[dd] * wy + CZ[dd] * wz));
+      g[j] = g[j] + (geq - g[j]) * P.inv_tau_g - W7[j] * delta;
+    }
+  }
+  return delta;
+}
+
+// FP64 block sum -> cumulative total acc[0] and this step's slot acc[2 + slot]
+__device__ __forceinline__ void block_delta_sum(double dsum, double *acc, int slot) {
   __shared__ double red[32];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   dsum = warp_sum(dsum);
@@ -680,6 +627,84 @@ __global__ void __launch_bounds__(128, CGLBM_MAIN_MINBLOCKS) k_main(Lattice L, S
   }
 }
 
+// a1, a2, a6 - a10 at fluid node (x, y, z) with link word lk, dense layout: pull,
+// curvature, collision, recolouring, reaction, transport, stores, outlet ghost.
+// Returns delta.
+__device__ __forceinline__ float main_node(const Lattice &L, const StepParams &P, const float *__restrict__ fin,
+                                           float *__restrict__ fout, const float4 *__restrict__ nrm, int x, int y,
+                                           int z, unsigned node, uint32_t lk, float *__restrict__ dbg_H,
+                                           float *__restrict__ dbg_delta) {
+  const unsigned ps = (unsigned)L.pstride;
+  PullOffsets O;
+  O.init(L, x, y, z);
+  StencilOffsets S;
+  S.init(L, x, y, z);
+  // a6 first, so that its loads do not overlap the 45 live populations
+  const float4 nme = nrm[node];
+  const float H =
+      nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nrm[S.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
+  // a1: pull with bounce-back
+  float fr[Q], fp[Q], g[Q7];
+  {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const bool bb = (lk >> i) & 1u;
+      const unsigned off = bb ? O.own : O.src(CX[i], CY[i], CZ[i]);
+      const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
+      fr[i] = fin[pr * ps + off];
+      fp[i] = fin[(pr + Q) * ps + off];
+    }
+    if (P.reaction_mode == 0) {
+#pragma unroll
+      for (int j = 0; j < Q7; ++j) {
+        const int d = GDIR[j];
+        const bool bb = (lk >> d) & 1u;
+        const unsigned off = bb ? O.own : O.src(CX[d], CY[d], CZ[d]);
+        const unsigned pj = bb ? (unsigned)GOPP[j] : (unsigned)j;
+        g[j] = fin[(2 * Q + pj) * ps + off];
+      }
+    }
+  }
+  const float delta = collide_node(P, lk, fr, fp, g, nme, H);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    fout[(unsigned)i * ps + O.own] = fr[i];
+    fout[(unsigned)(Q + i) * ps + O.own] = fp[i];
+  }
+  float g5 = 0.f;
+  if (P.reaction_mode == 0) {
+#pragma unroll
+    for (int j = 0; j < Q7; ++j) fout[(unsigned)(2 * Q + j) * ps + O.own] = g[j];
+    g5 = g[5];
+  } else {
+    g5 = fin[(unsigned)(2 * Q + 5) * ps + O.own];
+  }
+  if (L.bc_z == 1 && z == L.nz - 1) write_outlet_ghost(L, fout, x, y, fr, fp, g5, P.rho_out);
+  if (dbg_H) dbg_H[node] = H;
+  if (dbg_delta) dbg_delta[node] = delta;
+  return delta;
+}
+
+// Main update, dense layout, one thread per lattice node (used by the
+// allocation-free entry point).
+__global__ void __launch_bounds__(128, 5) k_main(Lattice L, StepParams P, const float *__restrict__ fin,
+                                              float *__restrict__ fout, const uint32_t *__restrict__ link,
+                                              const float4 *__restrict__ nrm, double *__restrict__ acc,
+                                              int slot, float *__restrict__ dbg_H, float *__restrict__ dbg_delta) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  double dsum = 0.0;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    acc[2 + (slot ^ 1)] = 0.0;   // clear the other per-step slot for the next step
+  const bool inside = x < L.nx && y < L.ny;
+  const unsigned node = inside ? (unsigned)nidx(L, x, y, z) : 0u;
+  const uint32_t lk = inside ? link[node] : BIT_SOLID;
+  if (!(lk & BIT_SOLID))
+    dsum = (double)main_node(L, P, fin, fout, nrm, x, y, z, node, lk, dbg_H, dbg_delta);
+  block_delta_sum(dsum, acc, slot);
+}
+
 // ---------------------------------------------------------------------------
 // a11: observables of the stored state (FP64 block reductions)
 // ---------------------------------------------------------------------------
@@ -693,23 +718,24 @@ __global__ void k_observables(Lattice L, const float *__restrict__ f, const uint
   const bool inside = x < L.nx && y < L.ny;
   const long long node = inside ? nidx(L, x, y, z) : 0;
   if (inside && !(link[node] & BIT_SOLID)) {
-    double rr = 0.0, rp = 0.0, cc = 0.0, jz = 0.0;
+    // per-node sums in FP32 (19 terms), accumulation over the lattice in FP64
+    float rr = 0.f, rp = 0.f, cc = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double a = f[pidx(L, i, z + 1, y, x)], b = f[pidx(L, Q + i, z + 1, y, x)];
+      const float a = f[pidx(L, i, z + 1, y, x)], b = f[pidx(L, Q + i, z + 1, y, x)];
       rr += a;
       rp += b;
       if (CZ[i]) jz += CZ[i] * (a + b);
     }
 #pragma unroll
     for (int j = 0; j < Q7; ++j) cc += f[pidx(L, 2 * Q + j, z + 1, y, x)];
-    const double rho = rr + rp;
+    const float rho = rr + rp;
     v[0] = rr;
     v[1] = rp;
     v[2] = cc;
-    const bool bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(cc);
+    const bool bad = !(rho > 0.f) || !isfinite(rho) || !isfinite(cc);
     if (!bad) {
-      v[3] = 0.5 * (1.0 - (rr - rp) / rho);
+      v[3] = 0.5f * (1.0f - (rr - rp) / rho);
       if (z == 0) v[4] = jz / rho * cc;
       if (z == L.nz - 1) v[5] = jz / rho * cc;
     }

@@ -114,6 +114,32 @@ struct PullOffsets {
   }
 };
 
+// 32-bit node-index offsets of the stencil neighbours x + c (periodic x, y; z
+// periodic or clamped), for fields indexed by node: own + dx[cx+1] + dy[cy+1] + dz[cz+1]
+struct StencilOffsets {
+  unsigned own;
+  int dx[3], dy[3], dz[3];
+  __device__ __forceinline__ void init(const Lattice &L, int x, int y, int z) {
+    const int plane = (int)L.plane;
+    own = (unsigned)(z * plane + y * L.nx + x);
+    dx[1] = dy[1] = dz[1] = 0;
+    dx[0] = x > 0 ? -1 : L.nx - 1;
+    dx[2] = x + 1 < L.nx ? 1 : 1 - L.nx;
+    dy[0] = y > 0 ? -L.nx : (L.ny - 1) * L.nx;
+    dy[2] = y + 1 < L.ny ? L.nx : (1 - L.ny) * L.nx;
+    if (L.bc_z == 0) {
+      dz[0] = z > 0 ? -plane : (L.nz - 1) * plane;
+      dz[2] = z + 1 < L.nz ? plane : (1 - L.nz) * plane;
+    } else {
+      dz[0] = z > 0 ? -plane : 0;
+      dz[2] = z + 1 < L.nz ? plane : 0;
+    }
+  }
+  __device__ __forceinline__ unsigned nb(int cx, int cy, int cz) const {
+    return own + (unsigned)(dx[cx + 1] + dy[cy + 1] + dz[cz + 1]);
+  }
+};
+
 // stored-plane index of the pull source z - cz: periodic wrap, or the ghost
 // planes 0 / nz + 1 in column mode
 __device__ __forceinline__ void pull_planes(const Lattice &L, int z, int zp_src[3]) {

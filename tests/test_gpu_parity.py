@@ -82,9 +82,14 @@ def test_geometry_fields(bc):
 # --------------------------------------------------------------------- one step
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_single_step_random_state(bc, mode):
-    """Ragged box (x, y not multiples of the block), random mask and non-equilibrium state."""
-    shape = (19, 21, 37)
+@pytest.mark.parametrize("nx", [37, 36])
+def test_single_step_random_state(bc, mode, nx):
+    """Ragged box, random mask and non-equilibrium state.
+
+    nx = 37 runs the one-thread-per-node main kernel, nx = 36 the row-staged one
+    (rows of 36 floats staged by bulk copies; y = 21 is not a multiple of the block).
+    """
+    shape = (19, 21, nx)
     rng = np.random.default_rng(100 + bc + 2 * mode)
     solid = rng.random(shape) < 0.3
     p = lbm.Params(sigma=0.05, theta_deg=60.0, accel=(1e-4, -2e-5, 3e-5), k_rate=0.05, xi=0.4,

@@ -27,7 +27,7 @@ struct lbm_ctx {
   float4 *ns = nullptr;
   float *rhoN = nullptr;
   float4 *nrm = nullptr;
-  uint32_t *bnd_list = nullptr;         // solid nodes next to the fluid
+  uint32_t *bnd_list = nullptr;         // solid nodes next to the fluid, packed (x, y, z)
   long long n_bnd = 0;
   double *acc = nullptr;                // [0] cumulative delta, [2 + s] per-step delta slots
   double *obs = nullptr;                // 8 observables accumulators
@@ -198,7 +198,7 @@ int launch_step(lbm_ctx *c) {
     prof_end(c);
   }
   prof_begin(c, 4);
-  k_main_c<<<(unsigned)((c->C.nf + 127) / 128), 128, 0, c->stream>>>(
+  k_main_c<<<(unsigned)((c->C.nf + CGLBM_MAIN_BLOCK - 1) / CGLBM_MAIN_BLOCK), CGLBM_MAIN_BLOCK, 0, c->stream>>>(
       L, c->C, c->sp, c->fa, c->fb, c->gidx, c->cnode, c->link, c->nrm, c->acc, slot,
       c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
   prof_end(c);
@@ -394,10 +394,10 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
   std::vector<uint32_t> blist, cnode;
   std::vector<int> gidx((size_t)L.plane * (L.nz + 2), -1);
   for (long long i = 0; i < n; ++i) {
-    if (hlink[i] & BIT_SOLID_BND) blist.push_back((uint32_t)i);
+    const uint32_t x = (uint32_t)(i % L.nx), y = (uint32_t)((i / L.nx) % L.ny), z = (uint32_t)(i / L.plane);
+    if (hlink[i] & BIT_SOLID_BND) blist.push_back(x | (y << 10) | (z << 20));
     if (hlink[i] & BIT_WALL) c->n_wall++;
     if (!(hlink[i] & BIT_SOLID)) {
-      const uint32_t x = (uint32_t)(i % L.nx), y = (uint32_t)((i / L.nx) % L.ny), z = (uint32_t)(i / L.plane);
       gidx[(size_t)(i + L.plane)] = (int)cnode.size();
       c->h_slot_node.push_back((uint32_t)i);
       cnode.push_back(x | (y << 10) | (z << 20));

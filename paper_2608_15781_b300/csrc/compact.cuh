@@ -13,6 +13,17 @@
 #pragma once
 #include "kernels.cuh"
 
+// launch shapes (the defaults are the measured best on B300)
+#ifndef CGLBM_MAIN_BLOCK
+#define CGLBM_MAIN_BLOCK 128
+#endif
+#ifndef CGLBM_MAIN_MINB
+#define CGLBM_MAIN_MINB 8
+#endif
+#ifndef CGLBM_DENS_MINB
+#define CGLBM_DENS_MINB 1
+#endif
+
 namespace cglbm {
 
 struct Compact {
@@ -58,7 +69,7 @@ __device__ __forceinline__ void pull_compact(const Lattice &L, const Compact &C,
 }
 
 // a1 + a2 over the fluid slots: colour function rho^N (dense field)
-__global__ void __launch_bounds__(256) k_density_c(Lattice L, Compact C, const float *__restrict__ f,
+__global__ void __launch_bounds__(256, CGLBM_DENS_MINB) k_density_c(Lattice L, Compact C, const float *__restrict__ f,
                                                    const int *__restrict__ gidx, const uint32_t *__restrict__ cnode,
                                                    float *__restrict__ rhoN) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,7 +147,7 @@ __device__ __forceinline__ void write_outlet_ghost_c(const Compact &C, float *__
 }
 
 // a1, a2, a6 - a10 over the fluid slots; stores are coalesced and whole-sector
-__global__ void __launch_bounds__(128, 5) k_main_c(Lattice L, Compact C, StepParams P,
+__global__ void __launch_bounds__(CGLBM_MAIN_BLOCK, CGLBM_MAIN_MINB) k_main_c(Lattice L, Compact C, StepParams P,
                                                    const float *__restrict__ fin, float *__restrict__ fout,
                                                    const int *__restrict__ gidx, const uint32_t *__restrict__ cnode,
                                                    const uint32_t *__restrict__ link,

@@ -212,9 +212,11 @@ __global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8
   uint32_t bits = 0;
   float4 nsv = make_float4(0.f, 0.f, 0.f, 0.f);
   if (solid[node]) {
+    // solid node: bit i set if x + c_i is fluid (stencil rules), used by the
+    // solid-colour and solid-normal averages
     bits = BIT_SOLID;
     for (int i = 0; i < Q - 1; ++i)
-      if (!solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i])) bits |= BIT_SOLID_BND;
+      if (!solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i])) bits |= BIT_SOLID_BND | (1u << i);
   } else {
     // bounce-back links: the pull source x - c_i is solid (column ghosts are fluid)
     for (int i = 0; i < Q - 1; ++i) {
@@ -375,27 +377,27 @@ __global__ void __launch_bounds__(256) k_density(Lattice L, const float *__restr
   rhoN[node] = (rr - rp) / (rr + rp);
 }
 
-// a3: Eq. color_lattice_weighted_average at solid nodes next to the fluid
+// a3: Eq. color_lattice_weighted_average at solid nodes next to the fluid.
+// list holds packed x | y << 10 | z << 20; a solid node's link word marks in
+// bit i whether x + c_i is fluid.
 __global__ void k_color_solid(Lattice L, const uint32_t *__restrict__ list, long long count,
                               const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const long long s = list[t];
-  const int z = (int)(s / L.plane);
-  const long long rem = s - (long long)z * L.plane;
-  const int y = (int)(rem / L.nx), x = (int)(rem - (long long)y * L.nx);
-  Stencil S;
+  const uint32_t pk = list[t];
+  const int x = (int)(pk & 1023u), y = (int)((pk >> 10) & 1023u), z = (int)((pk >> 20) & 2047u);
+  StencilOffsets S;
   S.init(L, x, y, z);
+  const uint32_t lk = link[S.own];
   float num = 0.f, den = 0.f;
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) {
-    const long long nb = S.nb(L, CX[i], CY[i], CZ[i]);
-    if (!(link[nb] & BIT_SOLID)) {
-      num += W[i] * rhoN[nb];
+    if ((lk >> i) & 1u) {
+      num += W[i] * rhoN[S.nb(CX[i], CY[i], CZ[i])];
       den += W[i];
     }
   }
-  rhoN[s] = den > 0.f ? num / den : 0.f;
+  rhoN[S.own] = den > 0.f ? num / den : 0.f;
 }
 
 // a4 + a5 from the gradient (gx, gy, gz): n = +grad/|grad| (reading of
@@ -472,18 +474,16 @@ __global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, lon
                                const uint32_t *__restrict__ link, float4 *__restrict__ nrm) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const long long s = list[t];
-  const int z = (int)(s / L.plane);
-  const long long rem = s - (long long)z * L.plane;
-  const int y = (int)(rem / L.nx), x = (int)(rem - (long long)y * L.nx);
-  Stencil S;
+  const uint32_t pk = list[t];
+  const int x = (int)(pk & 1023u), y = (int)((pk >> 10) & 1023u), z = (int)((pk >> 20) & 2047u);
+  StencilOffsets S;
   S.init(L, x, y, z);
+  const uint32_t lk = link[S.own];
   float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) {
-    const long long nb = S.nb(L, CX[i], CY[i], CZ[i]);
-    if (!(link[nb] & BIT_SOLID)) {
-      const float4 v = nrm[nb];
+    if ((lk >> i) & 1u) {
+      const float4 v = nrm[S.nb(CX[i], CY[i], CZ[i])];
       ax += W[i] * v.x;
       ay += W[i] * v.y;
       az += W[i] * v.z;
@@ -492,15 +492,12 @@ __global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, lon
   const float m = sqrtf(ax * ax + ay * ay + az * az);
   if (m >= GRAD_EPS) {
     const float inv = 1.0f / m;
-    nrm[s] = make_float4(ax * inv, ay * inv, az * inv, 0.f);
+    nrm[S.own] = make_float4(ax * inv, ay * inv, az * inv, 0.f);
   } else {
-    nrm[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    nrm[S.own] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
-// ---------------------------------------------------------------------------
-// a1, a2, a6 - a10: the fused main update
-// ---------------------------------------------------------------------------
 // a6: H = -sum_ab (delta_ab - n_a n_b) d_a n_b, d_a n_b by Eq. finite_difference_scheme;
 // nb(i) returns the normal at x + c_i
 template <class NbNormal>

@@ -86,7 +86,8 @@ typedef struct {
   double xi;          /* reaction rate of the paper's mode (Eq. reactive_boundary_condition_*) */
   int32_t reaction_mode; /* 0: delta = min(k NN r C psi, C, rho^r), C on D3Q7;
                             1: delta = min(xi NN r, 1) rho^r, C not evolved                  */
-  int32_t storage;    /* population storage: 0 = FP32 (only value accepted)                  */
+  int32_t storage;    /* population storage: 0 = FP32; 1 = FP16 deviations from the resting
+                         reactant equilibrium (f^r - w, f^p, g - w), FP32 arithmetic          */
   void *cuda_stream;  /* cudaStream_t to launch on (borrowed); NULL = legacy default stream  */
 } lbm_params;
 

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "cglbm.h"
@@ -22,7 +23,8 @@ struct lbm_ctx {
   StepParams sp{};
   cudaStream_t stream = nullptr;
   // device memory (library-owned)
-  float *fa = nullptr, *fb = nullptr;   // current / next populations, compact layout [45][C.ns]
+  void *fa = nullptr, *fb = nullptr;    // current / next populations, compact layout [45][C.ns]
+  bool half = false;                    // FP16 deviation storage (lbm_params.storage = 1)
   uint32_t *link = nullptr;
   float4 *ns = nullptr;
   float *rhoN = nullptr;
@@ -116,7 +118,7 @@ int check_params(const lbm_params *p) {
   if (!(p->diffusivity > 0.0) || !std::isfinite(p->diffusivity)) return LBM_EINVAL;
   if (!(p->beta >= 0.0) || !std::isfinite(p->sigma) || !std::isfinite(p->theta_deg)) return LBM_EINVAL;
   if (p->reaction_mode != 0 && p->reaction_mode != 1) return LBM_EINVAL;
-  if (p->storage != 0) return LBM_EINVAL;
+  if (p->storage != 0 && p->storage != 1) return LBM_EINVAL;
   if (!(p->k_rate >= 0.0) || !(p->xi >= 0.0) || !(p->rho_out > 0.0)) return LBM_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->accel[a])) return LBM_EINVAL;
@@ -142,12 +144,24 @@ void fill_step_params(lbm_ctx *c) {
   s.reaction_mode = p.reaction_mode;
 }
 
+// run f<float>() or f<__half>() for the context's population storage
+template <class F>
+void with_storage(const lbm_ctx *c, F &&f) {
+  if (c->half)
+    f((__half *)nullptr);
+  else
+    f((float *)nullptr);
+}
+
 // reduce observables of the current state into c->obs (async)
 int launch_observables(lbm_ctx *c) {
   CK(cudaMemsetAsync(c->obs, 0, 8 * sizeof(double), c->stream));
   prof_begin(c, 5);
-  k_observables_c<<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(c->L, c->C, c->fa, c->cnode,
-                                                                             c->obs);
+  with_storage(c, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_observables_c<T><<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(c->L, c->C, (const T *)c->fa,
+                                                                                c->cnode, c->obs);
+  });
   prof_end(c);
   CK(cudaGetLastError());
   return LBM_OK;
@@ -158,8 +172,11 @@ int reset_after_state(lbm_ctx *c) {
   const Lattice &L = c->L;
   if (L.bc_z == 1) {
     dim3 b(32, 4, 1), g((L.nx + 31) / 32, (L.ny + 3) / 4, 1);
-    k_ghost_init_c<<<g, b, 0, c->stream>>>(L, c->C, c->gidx, (float)c->prm.u_in, (float)c->prm.c_in,
-                                           (float)c->prm.rho_out, c->fa, c->fb);
+    with_storage(c, [&](auto *tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      k_ghost_init_c<T><<<g, b, 0, c->stream>>>(L, c->C, c->gidx, (float)c->prm.u_in, (float)c->prm.c_in,
+                                                (float)c->prm.rho_out, (T *)c->fa, (T *)c->fb);
+    });
     CK(cudaGetLastError());
   }
   CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(double), c->stream));
@@ -180,7 +197,10 @@ int launch_step(lbm_ctx *c) {
   const int slot = (int)(c->step & 1);
   prof_begin(c, 0);
   const unsigned gf = (unsigned)((c->C.nf + 255) / 256);
-  k_density_c<<<gf, 256, 0, c->stream>>>(L, c->C, c->fa, c->gidx, c->cnode, c->rhoN);
+  with_storage(c, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_density_c<T><<<gf, 256, 0, c->stream>>>(L, c->C, (const T *)c->fa, c->gidx, c->cnode, c->rhoN);
+  });
   prof_end(c);
   if (c->n_bnd > 0) {
     const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
@@ -198,12 +218,15 @@ int launch_step(lbm_ctx *c) {
     prof_end(c);
   }
   prof_begin(c, 4);
-  k_main_c<<<(unsigned)((c->C.nf + CGLBM_MAIN_BLOCK - 1) / CGLBM_MAIN_BLOCK), CGLBM_MAIN_BLOCK, 0, c->stream>>>(
-      L, c->C, c->sp, c->fa, c->fb, c->gidx, c->cnode, c->link, c->nrm, c->acc, slot,
-      c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
+  with_storage(c, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_main_c<T><<<(unsigned)((c->C.nf + CGLBM_MAIN_BLOCK - 1) / CGLBM_MAIN_BLOCK), CGLBM_MAIN_BLOCK, 0,
+                  c->stream>>>(L, c->C, c->sp, (const T *)c->fa, (T *)c->fb, c->gidx, c->cnode, c->link, c->nrm,
+                               c->acc, slot, c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
+  });
   prof_end(c);
   CK(cudaGetLastError());
-  float *t = c->fa;
+  void *t = c->fa;
   c->fa = c->fb;
   c->fb = t;
   c->step += 1;
@@ -411,7 +434,8 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
       gidx[(size_t)q] = c->C.nf + (int)q;                                         // inlet plane
       gidx[(size_t)((L.nz + 1) * L.plane + q)] = c->C.nf + (int)(L.plane + q);    // outlet plane
     }
-  const size_t pop_bytes = (size_t)NPOP * c->C.ns * sizeof(float);
+  c->half = params->storage == 1;
+  const size_t pop_bytes = (size_t)NPOP * c->C.ns * (c->half ? sizeof(__half) : sizeof(float));
   if (dalloc(c, (void **)&c->fa, pop_bytes) || dalloc(c, (void **)&c->fb, pop_bytes) ||
       dalloc(c, (void **)&c->gidx, gidx.size() * sizeof(int)) ||
       dalloc(c, (void **)&c->cnode, cnode.size() * sizeof(uint32_t)))
@@ -428,8 +452,12 @@ int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out
         cudaSuccess)
       return fail(LBM_ECUDA);
   }
-  k_init_c<<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
-      L, c->C, c->cnode, nullptr, nullptr, nullptr, nullptr, 1.0f, 0.0f, (float)params->c_init, c->fa, c->fb);
+  with_storage(c, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_init_c<T><<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
+        L, c->C, c->cnode, nullptr, nullptr, nullptr, nullptr, 1.0f, 0.0f, (float)params->c_init, (T *)c->fa,
+        (T *)c->fb);
+  });
   if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
   rc = reset_after_state(c);
   if (rc) return fail(rc);
@@ -515,8 +543,12 @@ int lbm_init_fields(lbm_ctx *c, const float *rho_r, const float *rho_p, const fl
     rc = cuda_fail(c, cudaErrorUnknown);
   if (!rc) {
     const float *fd = d;
-    k_init_c<<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
-        L, c->C, c->cnode, fd, fd + L.n, fd + 2 * L.n, u ? fd + 3 * L.n : nullptr, 0.f, 0.f, 0.f, c->fa, c->fb);
+    with_storage(c, [&](auto *tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      k_init_c<T><<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
+          L, c->C, c->cnode, fd, fd + L.n, fd + 2 * L.n, u ? fd + 3 * L.n : nullptr, 0.f, 0.f, 0.f, (T *)c->fa,
+          (T *)c->fb);
+    });
     if (cudaGetLastError() != cudaSuccess) rc = cuda_fail(c, cudaErrorLaunchFailure);
   }
   if (!rc) rc = reset_after_state(c);
@@ -532,16 +564,25 @@ int lbm_get_state(lbm_ctx *c, float *dst, size_t bytes) {
   if (c->sticky) return c->sticky;
   cudaSetDevice(c->device);
   const size_t nf = (size_t)c->C.nf;
+  float *d = nullptr;
+  if (cudaMalloc((void **)&d, (size_t)NPOP * nf * sizeof(float)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  with_storage(c, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_slots_to_f32<T><<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(c->C, (const T *)c->fa, d);
+  });
   std::vector<float> h((size_t)NPOP * nf);
-  for (int p = 0; p < NPOP; ++p)
-    CK(cudaMemcpyAsync(h.data() + (size_t)p * nf, c->fa + (size_t)p * c->C.ns, nf * sizeof(float),
-                       cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  cudaError_t e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(c, e);
   std::memset(dst, 0, bytes);   // solid nodes hold no populations
   for (int p = 0; p < NPOP; ++p) {
-    float *d = dst + (size_t)p * L.n;
+    float *o = dst + (size_t)p * L.n;
     const float *s = h.data() + (size_t)p * nf;
-    for (size_t t = 0; t < nf; ++t) d[c->h_slot_node[t]] = s[t];
+    for (size_t t = 0; t < nf; ++t) o[c->h_slot_node[t]] = s[t];
   }
   return LBM_OK;
 }
@@ -556,15 +597,24 @@ int lbm_set_state(lbm_ctx *c, const float *src, size_t bytes) {
   std::vector<float> h((size_t)NPOP * nf);
   for (int p = 0; p < NPOP; ++p) {
     const float *s = src + (size_t)p * L.n;
-    float *d = h.data() + (size_t)p * nf;
-    for (size_t t = 0; t < nf; ++t) d[t] = s[c->h_slot_node[t]];
+    float *o = h.data() + (size_t)p * nf;
+    for (size_t t = 0; t < nf; ++t) o[t] = s[c->h_slot_node[t]];
   }
-  for (int p = 0; p < NPOP; ++p) {
-    CK(cudaMemcpyAsync(c->fa + (size_t)p * c->C.ns, h.data() + (size_t)p * nf, nf * sizeof(float),
-                       cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->fb + (size_t)p * c->C.ns, h.data() + (size_t)p * nf, nf * sizeof(float),
-                       cudaMemcpyHostToDevice, c->stream));
+  float *d = nullptr;
+  if (cudaMalloc((void **)&d, h.size() * sizeof(float)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
   }
+  cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    with_storage(c, [&](auto *tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      k_f32_to_slots<T><<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(c->C, d, (T *)c->fa, (T *)c->fb);
+    });
+    e = cudaStreamSynchronize(c->stream);
+  }
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(c, e);
   return reset_after_state(c);
 }
 

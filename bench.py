@@ -14,6 +14,7 @@ Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on the host cores on bounded samples of the same workload instead.
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -42,6 +43,9 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",
+                    help="population storage of the headline run (the other is reported under variants)")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -144,13 +148,15 @@ class ClockSampler:
 def bytes_per_fluid_node(params):
     """Algorithmic bytes of one fluid-node update: populations read + written, plus 1 B of flags.
 
-    361 B with the reactant populations (45 FP32 values each way), 305 B in the
-    paper's reaction mode (38).  Solid nodes carry no populations (the library
+    FP32 storage: 361 B with the reactant populations (45 values each way), 305 B
+    in the paper's reaction mode (38); FP16 storage: 181 B / 153 B.  Solid nodes
+    carry no populations (the library
     stores the fluid nodes only), so a launch's algorithmic traffic is this
     figure times the number of fluid nodes.
     """
     npop = 45 if params.reaction_mode == 0 else 38
-    return 2 * 4 * npop + 1
+    width = 2 if params.storage == 1 else 4
+    return 2 * width * npop + 1
 
 
 # --------------------------------------------------------------------------- CPU oracle legs
@@ -240,52 +246,74 @@ def run_native(args):
     wl = WORKLOADS[args.workload]
     solid = wl.mask()
     stream = torch.cuda.current_stream()
-    L = lbm.Lattice(solid, wl.params, bc_z=wl.bc_z, stream=stream.cuda_stream)
-    info = L.info()
     N = wl.nodes
-    Nf = info["n_fluid"]
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    L.step(args.warmup)
-    barrier()
+    def max_over_ranks(v):
+        if world > 1:
+            tt = torch.tensor([v], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            v = float(tt.item())
+        return v
+
+    def measure(params, steps, warmup, clocks=None):
+        """K timed steps, per-kernel CUDA events on the launching stream; time = max over ranks."""
+        L = lbm.Lattice(solid, params, bc_z=wl.bc_z, stream=stream.cuda_stream)
+        info = L.info()
+        L.step(warmup)
+        barrier()
+        if clocks:
+            clocks.start()
+        L.profile(steps * 6 + 16)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop() if clocks else None
+        t = max_over_ranks(e0.elapsed_time(e1))
+        prof = L.profile_read()
+        L.profile(0)
+        ob = L.observables()
+        L.close()
+        return t, prof, info, ob, clk
+
+    def roofline(params, prof, nf):
+        kname = max(prof, key=lambda k: prof[k][0])
+        k_ms, k_n = prof[kname]
+        per_node = bytes_per_fluid_node(params)
+        alg = nf * per_node
+        return kname, per_node, alg, alg / (k_ms / k_n * 1e-3) / 1e9
+
+    peak, peak_kind = measured_peaks()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
-    clocks = ClockSampler(gpu_idx)
-    clocks.start()
-    # timed region: K steps, per-kernel CUDA events recorded on the launching stream
-    L.profile(args.steps * 6 + 16)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    L.step(args.steps)
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
-    prof = L.profile_read()
-    L.profile(0)
-    ob = L.observables()
-    L.close()
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    head = dataclasses.replace(wl.params, storage=1 if args.storage == "fp16" else 0)
+    t_ms, prof, info, ob, clk = measure(head, args.steps, args.warmup, ClockSampler(gpu_idx))
+    Nf = info["n_fluid"]
     value = world * N * args.steps / (t_ms * 1e-3) / 1e6
-
-    # dominant kernel and its roofline
-    kname = max(prof, key=lambda k: prof[k][0])
-    k_ms, k_n = prof[kname]
-    peak, peak_kind = measured_peaks()
-    per_node = bytes_per_fluid_node(wl.params)
-    alg_bytes = Nf * per_node
-    achieved = alg_bytes / (k_ms / k_n * 1e-3) / 1e9
-    traf = ncu_traffic_per_fluid_node() if kname == "main" else None
+    kname, per_node, alg_bytes, achieved = roofline(head, prof, Nf)
+    traf = ncu_traffic_per_fluid_node() if (kname == "main" and head.storage == 0) else None
     launches = int(sum(n for _, n in prof.values()))
+
+    variants = {}
+    if not args.no_variants:
+        other = dataclasses.replace(head, storage=1 - head.storage)
+        vsteps = max(args.steps // 2, 1)
+        tv, pv, _, obv, _ = measure(other, vsteps, args.warmup)
+        kv, pnv, _, achv = roofline(other, pv, Nf)
+        variants["fp16_storage" if other.storage == 1 else "fp32_storage"] = {
+            "value": round(world * N * vsteps / (tv * 1e-3) / 1e6, 2), "unit": UNIT, "steps": vsteps,
+            "ms_per_step": round(tv / vsteps, 5), "dtype": "f16 storage, f32 math" if other.storage else "f32",
+            "roofline": {"kernel": f"k_{kv}", "achieved": round(achv, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
+            "conversion": obv["conversion"], "gas_saturation": obv["gas_saturation"]}
 
     # end to end through the C ABI with host buffers: create from the host mask,
     # K x (step + read of the step's reaction sums), observables, destroy
@@ -294,18 +322,14 @@ def run_native(args):
         solid_h = np.ascontiguousarray(solid, dtype=np.uint8)
         barrier()
         t0 = time.perf_counter()
-        L2 = lbm.Lattice(solid_h, wl.params, bc_z=wl.bc_z, stream=stream.cuda_stream)
+        L2 = lbm.Lattice(solid_h, head, bc_z=wl.bc_z, stream=stream.cuda_stream)
         for _ in range(args.steps):
             L2.step(1)
             L2.reaction()
-        ob2 = L2.observables()
+        L2.observables()
         L2.close()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0)
         h2d = N * 1                                  # the mask
         d2h = 16 * args.steps + 4 * N + 8 * 8 * 2    # reaction sums per step, link readback, observables
         e2e = {"value": round(world * N * args.steps / te / 1e6, 2), "unit": UNIT,
@@ -315,18 +339,19 @@ def run_native(args):
 
     if rank != 0:
         return 0
-    kern = {k: {"ms_total": round(v[0], 3), "launches": v[1],
-                "share": round(v[0] / max(sum(x[0] for x in prof.values()), 1e-9), 4)} for k, v in prof.items()}
+    tot = max(sum(x[0] for x in prof.values()), 1e-9)
+    kern = {k: {"ms_total": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)} for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16" if head.storage else "f32", "data": "synthetic",
         "config": {"workload": wl.name, "lattice_xyz": [wl.shape[2], wl.shape[1], wl.shape[0]],
                    "mask": f"GRF shell |k|={wl.shell_k0}+-1, porosity {wl.porosity}, seed {wl.seed}",
                    "fluid_nodes": Nf, "porosity": round(Nf / N, 4),
                    "boundaries": "inlet/outlet in z" if wl.bc_z else "periodic",
+                   "storage": "fp16 deviations" if head.storage else "fp32",
                    "fluid_mlups": round(world * Nf * args.steps / (t_ms * 1e-3) / 1e6, 2),
-                   "l2": "state (2 x 45 x N x 4 B) far above the 126 MB L2; no flush",
+                   "l2": "state (2 x 45 x fluid nodes x 4 B) far above the 126 MB L2; no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": f"k_{kname}", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -338,6 +363,7 @@ def run_native(args):
                      else "fallback 6.4 TB/s",
                      "step_effective_gbs": round(alg_bytes / (t_ms / args.steps * 1e-3) / 1e9, 1)},
         "kernels": kern,
+        "variants": variants,
         "gpu_launches": launches,
         "clocks": clk,
         "observables": {k: ob[k] for k in ("mass_r", "mass_p", "conversion", "gas_saturation", "n_bad")},

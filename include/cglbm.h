@@ -124,7 +124,9 @@ typedef struct {
  * C = c_init.  *out is set only on success. */
 int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out);
 
-/* Advance nsteps >= 0 time steps, asynchronously on the context's stream. */
+/* Advance nsteps >= 0 time steps, asynchronously on the context's stream.
+ * Unless profiling or debug output is on, each step is replayed from a CUDA
+ * graph built at the first call (one graph launch per step). */
 int lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Reduce the observables of the current (post-collision) state in FP64 on the
@@ -163,6 +165,12 @@ int lbm_set_debug(lbm_ctx *ctx, int32_t enable);
 int lbm_profile(lbm_ctx *ctx, int32_t enable);
 int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
+/* Pick the launch shapes of the main, colour-function and normal kernels by
+ * timing each candidate (main: 64/128/256 threads; others 128/256/512) on the
+ * current state; blocks[3] (may be NULL) receives the choice.  The state is not
+ * advanced.  Without a call the defaults (128, 256, 256) are used. */
+int lbm_tune(lbm_ctx *ctx, int32_t *blocks);
+
 /* Static counts: fluid nodes, wall nodes, solid nodes next to the fluid,
  * device bytes held.  Any pointer may be NULL. */
 int lbm_info(lbm_ctx *ctx, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd,
@@ -170,6 +178,28 @@ int lbm_info(lbm_ctx *ctx, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_b
 
 /* Release every device resource of the context; NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent lattices of different sizes, masks and parameters
+ * (e.g. a sweep over structures, contact angles or inlet velocities) advanced
+ * together: every kernel of a time step is one launch over the fluid nodes of
+ * all lattices, and a step is replayed as one CUDA graph.  Geometry k and
+ * params k describe lattice k exactly as for lbm_create; all params must use
+ * the same storage.  cuda_stream (borrowed) is used for every launch.
+ * lbm_batch_set_state replaces lattice k's state and, as for lbm_set_state,
+ * restarts the step counter and the reaction sums of the whole batch.
+ * lbm_batch_observables fills count = n entries, one per lattice. */
+typedef struct lbm_batch lbm_batch;   /* opaque, library-owned */
+int lbm_batch_create(int32_t n, const lbm_geometry *geoms, const lbm_params *params, void *cuda_stream,
+                     lbm_batch **out);
+int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
+int lbm_batch_observables(lbm_batch *batch, lbm_obs *out, int32_t count);
+int lbm_batch_get_state(lbm_batch *batch, int32_t k, float *host_dst, size_t bytes);
+int lbm_batch_set_state(lbm_batch *batch, int32_t k, const float *host_src, size_t bytes);
+int lbm_batch_tune(lbm_batch *batch, int32_t *blocks);
+int lbm_batch_profile(lbm_batch *batch, int32_t max_launches);
+int lbm_batch_profile_read(lbm_batch *batch, double *ms, int64_t *launches, int32_t n);
+void lbm_batch_destroy(lbm_batch *batch);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this entry point exists

@@ -1,7 +1,11 @@
-// Host side of the C ABI declared in include/cglbm.h: context, device memory,
-// launch sequence of one time step, observables, state transfer, profiling.
+// Host side of the C ABI declared in include/cglbm.h: batches of lattices in the
+// compact slot layout (a single context is a batch of one), the launch sequence
+// of one time step (optionally replayed as a CUDA graph), observables, state
+// transfer, launch-shape tuning, profiling, and the allocation-free step.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -16,37 +20,50 @@
 
 using namespace cglbm;
 
-struct lbm_ctx {
-  int device = 0;
-  Lattice L{};
+namespace {
+
+struct InstHost {
+  Inst d{};                           // the instance's device-table entry
   lbm_params prm{};
-  StepParams sp{};
+  long long n_fluid = 0, n_wall = 0, n_bnd = 0;
+  double mc0 = 0.0;                   // reactant mass when the state was set
+  std::vector<uint32_t> slot_node;    // local fluid slot -> node index
+};
+
+// One or more independent lattices sharing one slot space (see compact.cuh).
+struct Batch {
+  int device = 0;
   cudaStream_t stream = nullptr;
-  // device memory (library-owned)
-  void *fa = nullptr, *fb = nullptr;    // current / next populations, compact layout [45][C.ns]
-  bool half = false;                    // FP16 deviation storage (lbm_params.storage = 1)
+  bool half = false;                  // FP16 deviation storage
+  int n = 0;
+  std::vector<InstHost> h;
+  // slot space
+  Inst *inst = nullptr;
+  uint16_t *kid = nullptr;            // instance of each slot (null for one instance)
+  uint32_t *node = nullptr;           // packed coordinates of each slot
+  int nslots = 0, ns = 0;
+  void *fa = nullptr, *fb = nullptr, *buf0 = nullptr, *buf1 = nullptr;
+  int *gidx = nullptr;
+  // dense per-node fields of all instances
   uint32_t *link = nullptr;
-  float4 *ns = nullptr;
+  float4 *nsv = nullptr, *nrm = nullptr;
   float *rhoN = nullptr;
-  float4 *nrm = nullptr;
-  uint32_t *bnd_list = nullptr;         // solid nodes next to the fluid, packed (x, y, z)
-  long long n_bnd = 0;
-  double *acc = nullptr;                // [0] cumulative delta, [2 + s] per-step delta slots
-  double *obs = nullptr;                // 8 observables accumulators
-  int *err = nullptr;                   // device error flag (a bounded wait gave up)
-  Compact C{};                          // fluid slots and slot stride
-  int *gidx = nullptr;                  // stored lattice position -> slot, -1 = solid
-  uint32_t *cnode = nullptr;            // slot -> packed (x, y, z), fluid slots only
-  std::vector<uint32_t> h_slot_node;    // slot -> node index (host, for state transfer)
+  long long nodes = 0;
+  uint32_t *bnd = nullptr;
+  uint16_t *bnd_kid = nullptr;
+  int n_bnd = 0;
+  double *acc = nullptr, *acc_scratch = nullptr, *obs = nullptr;
+  int *err = nullptr;
   float *dbg_H = nullptr, *dbg_delta = nullptr;
   bool debug = false;
   size_t device_bytes = 0;
-  // host-side bookkeeping
   int64_t step = 0;
-  double mc0 = 0.0;
-  long long n_fluid = 0, n_wall = 0;
-  bool have_fields = false;             // rhoN / nrm hold the last step's values
   int sticky = LBM_OK;
+  // launch shapes (lbm_tune picks them by timing)
+  int main_block = 128, dens_block = 256, norm_block = 256;
+  // CUDA graphs of one step, for even and odd steps
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graphs_valid = false;
   // profiling
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
@@ -54,62 +71,71 @@ struct lbm_ctx {
   bool profiling = false;
 };
 
+}  // namespace
+
+struct lbm_ctx {
+  Batch b;
+};
+struct lbm_batch {
+  Batch b;
+};
+
 namespace {
 
-int cuda_fail(lbm_ctx *c, cudaError_t e) {
+int cuda_fail(Batch &b, cudaError_t e) {
   if (e == cudaSuccess) return LBM_OK;
-  if (c) c->sticky = LBM_ECUDA;
+  b.sticky = LBM_ECUDA;
   return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
 }
 
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(c, e_); \
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(b, e_);  \
   } while (0)
 
-int dalloc(lbm_ctx *c, void **p, size_t bytes) {
+int dalloc(Batch &b, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
     (void)cudaGetLastError();
     return LBM_ENOMEM;
   }
-  c->device_bytes += bytes;
+  b.device_bytes += bytes;
   return LBM_OK;
 }
 
 dim3 node_block() { return dim3(32, 4, 1); }
 dim3 node_grid(const Lattice &L) { return dim3((L.nx + 31) / 32, (L.ny + 3) / 4, L.nz); }
 
-void prof_begin(lbm_ctx *c, int kind) {
-  if (!c->profiling || c->ev_used + 2 > c->ev.size()) return;
-  cudaEventRecord(c->ev[c->ev_used], c->stream);
-  c->ev_kind[c->ev_used / 2] = kind;
+void prof_begin(Batch &b, int kind, cudaStream_t st) {
+  if (!b.profiling || b.ev_used + 2 > b.ev.size()) return;
+  cudaEventRecord(b.ev[b.ev_used], st);
+  b.ev_kind[b.ev_used / 2] = kind;
 }
-void prof_end(lbm_ctx *c) {
-  if (!c->profiling || c->ev_used + 2 > c->ev.size()) return;
-  cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
-  c->ev_used += 2;
+void prof_end(Batch &b, cudaStream_t st) {
+  if (!b.profiling || b.ev_used + 2 > b.ev.size()) return;
+  cudaEventRecord(b.ev[b.ev_used + 1], st);
+  b.ev_used += 2;
 }
 
-void free_all(lbm_ctx *c) {
-  cudaFree(c->fa);
-  cudaFree(c->fb);
-  cudaFree(c->link);
-  cudaFree(c->ns);
-  cudaFree(c->rhoN);
-  cudaFree(c->nrm);
-  cudaFree(c->bnd_list);
-  cudaFree(c->acc);
-  cudaFree(c->obs);
-  cudaFree(c->err);
-  cudaFree(c->gidx);
-  cudaFree(c->cnode);
-  cudaFree(c->dbg_H);
-  cudaFree(c->dbg_delta);
-  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  c->ev.clear();
+void drop_graphs(Batch &b) {
+  for (auto &g : b.graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  b.graphs_valid = false;
+}
+
+void free_all(Batch &b) {
+  drop_graphs(b);
+  void *ptrs[] = {b.inst, b.kid, b.node, b.buf0, b.buf1, b.gidx, b.link, b.nsv, b.nrm, b.rhoN, b.bnd, b.bnd_kid,
+                  b.acc, b.acc_scratch, b.obs, b.err, b.dbg_H, b.dbg_delta};
+  for (void *p : ptrs) cudaFree(p);
+  for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
+  b.ev.clear();
 }
 
 int check_params(const lbm_params *p) {
@@ -125,9 +151,18 @@ int check_params(const lbm_params *p) {
   return LBM_OK;
 }
 
-void fill_step_params(lbm_ctx *c) {
-  const lbm_params &p = c->prm;
-  StepParams &s = c->sp;
+int check_geometry(const lbm_geometry *g) {
+  if (!g || !g->solid) return LBM_EINVAL;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_EINVAL;
+  if (g->bc_z != 0 && g->bc_z != 1) return LBM_EINVAL;
+  if (g->bc_z == 1 && g->nz < 2) return LBM_EINVAL;
+  // packed slot coordinates (10 + 10 + 11 bits)
+  if (g->nx > 1024 || g->ny > 1024 || g->nz > 2048) return LBM_EINVAL;
+  return LBM_OK;
+}
+
+StepParams make_step_params(const lbm_params &p) {
+  StepParams s{};
   s.omega_cm = (float)(1.0 - 1.0 / p.tau);
   s.half_sigma = (float)(0.5 * p.sigma);
   s.beta = (float)p.beta;
@@ -142,95 +177,663 @@ void fill_step_params(lbm_ctx *c) {
   s.xi = (float)p.xi;
   s.rho_out = (float)p.rho_out;
   s.reaction_mode = p.reaction_mode;
+  return s;
 }
 
-// run f<float>() or f<__half>() for the context's population storage
+Lattice make_lattice(const lbm_geometry &g) {
+  Lattice L{};
+  L.nx = g.nx;
+  L.ny = g.ny;
+  L.nz = g.nz;
+  L.bc_z = g.bc_z;
+  L.n = (long long)g.nx * g.ny * g.nz;
+  L.plane = (long long)g.nx * g.ny;
+  L.pstride = L.plane * (g.nz + 2);
+  return L;
+}
+
+// run f((T *)nullptr) with T the batch's population storage type
 template <class F>
-void with_storage(const lbm_ctx *c, F &&f) {
-  if (c->half)
+void with_storage(const Batch &b, F &&f) {
+  if (b.half)
     f((__half *)nullptr);
   else
     f((float *)nullptr);
 }
 
-// reduce observables of the current state into c->obs (async)
-int launch_observables(lbm_ctx *c) {
-  CK(cudaMemsetAsync(c->obs, 0, 8 * sizeof(double), c->stream));
-  prof_begin(c, 5);
-  with_storage(c, [&](auto *tag) {
+Slots slots(const Batch &b) { return Slots{b.inst, b.kid, b.node, b.nslots, b.ns}; }
+
+template <typename T>
+void launch_density(const Batch &b, cudaStream_t st, const void *fin) {
+  const Slots S = slots(b);
+  switch (b.dens_block) {
+    case 128: k_density_c<T, 128><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, (const T *)fin, b.gidx, b.rhoN); break;
+    case 512: k_density_c<T, 512><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, (const T *)fin, b.gidx, b.rhoN); break;
+    default: k_density_c<T, 256><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, (const T *)fin, b.gidx, b.rhoN);
+  }
+}
+
+void launch_normal(const Batch &b, cudaStream_t st) {
+  const Slots S = slots(b);
+  switch (b.norm_block) {
+    case 128: k_normal_c<128><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, b.rhoN, b.link, b.nsv, b.nrm); break;
+    case 512: k_normal_c<512><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, b.rhoN, b.link, b.nsv, b.nrm); break;
+    default: k_normal_c<256><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, b.rhoN, b.link, b.nsv, b.nrm);
+  }
+}
+
+template <typename T>
+void launch_main(const Batch &b, cudaStream_t st, const void *fin, void *fout, double *acc, int slot) {
+  const Slots S = slots(b);
+  float *dh = b.debug ? b.dbg_H : nullptr, *dd = b.debug ? b.dbg_delta : nullptr;
+  switch (b.main_block) {
+    case 64:
+      k_main_c<T, 64><<<(S.nslots + 63) / 64, 64, 0, st>>>(S, b.n, (const T *)fin, (T *)fout, b.gidx, b.link, b.nrm,
+                                                          acc, slot, dh, dd);
+      break;
+    case 256:
+      k_main_c<T, 256><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, b.n, (const T *)fin, (T *)fout, b.gidx, b.link,
+                                                              b.nrm, acc, slot, dh, dd);
+      break;
+    default:
+      k_main_c<T, 128><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, b.n, (const T *)fin, (T *)fout, b.gidx, b.link,
+                                                              b.nrm, acc, slot, dh, dd);
+  }
+}
+
+// the kernels of one step (in -> out), on stream st
+void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int slot, bool prof) {
+  auto pb = [&](int k) { if (prof) prof_begin(b, k, st); };
+  auto pe = [&]() { if (prof) prof_end(b, st); };
+  with_storage(b, [&](auto *tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
-    k_observables_c<T><<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(c->L, c->C, (const T *)c->fa,
-                                                                                c->cnode, c->obs);
+    pb(0);
+    launch_density<T>(b, st, fin);
+    pe();
+    if (b.n_bnd > 0) {
+      pb(1);
+      k_color_solid_c<<<(b.n_bnd + 255) / 256, 256, 0, st>>>(b.inst, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+      pe();
+    }
+    pb(2);
+    launch_normal(b, st);
+    pe();
+    if (b.n_bnd > 0) {
+      pb(3);
+      k_normal_solid_c<<<(b.n_bnd + 255) / 256, 256, 0, st>>>(b.inst, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+      pe();
+    }
+    pb(4);
+    launch_main<T>(b, st, fin, fout, b.acc, slot);
+    pe();
   });
-  prof_end(c);
+}
+
+// two graphs of one step: even steps read buf0 and write buf1, odd steps the reverse
+int build_graphs(Batch &b) {
+  drop_graphs(b);
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int rc = LBM_OK;
+  for (int parity = 0; parity < 2 && rc == LBM_OK; ++parity) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = LBM_ECUDA;
+      break;
+    }
+    enqueue_step(b, cs, parity ? b.buf1 : b.buf0, parity ? b.buf0 : b.buf1, parity, false);
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) {
+      rc = LBM_ECUDA;
+      break;
+    }
+    if (cudaGraphInstantiate(&b.graph[parity], g, 0) != cudaSuccess) rc = LBM_ECUDA;
+    cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  if (rc != LBM_OK) {
+    (void)cudaGetLastError();
+    drop_graphs(b);
+    return LBM_OK;   // graphs are an optimisation: fall back to plain launches
+  }
+  b.graphs_valid = true;
+  return LBM_OK;
+}
+
+int launch_observables(Batch &b) {
+  CK(cudaMemsetAsync(b.obs, 0, 8 * sizeof(double) * b.n, b.stream));
+  prof_begin(b, 5, b.stream);
+  with_storage(b, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_observables_c<T><<<(b.nslots + 255) / 256, 256, 0, b.stream>>>(slots(b), (const T *)b.fa, b.obs);
+  });
+  prof_end(b, b.stream);
   CK(cudaGetLastError());
   return LBM_OK;
 }
 
-// after the state changed: ghost planes, counters, m^C(0)
-int reset_after_state(lbm_ctx *c) {
-  const Lattice &L = c->L;
-  if (L.bc_z == 1) {
-    dim3 b(32, 4, 1), g((L.nx + 31) / 32, (L.ny + 3) / 4, 1);
-    with_storage(c, [&](auto *tag) {
+// after the state changed (it is in both buffers): buffer order, ghost planes, counters, m^C(0)
+int reset_after_state(Batch &b) {
+  b.fa = b.buf0;
+  b.fb = b.buf1;
+  for (int k = 0; k < b.n; ++k) {
+    const Inst &I = b.h[k].d;
+    if (I.L.bc_z != 1) continue;
+    const dim3 blk(32, 4, 1), grd((I.L.nx + 31) / 32, (I.L.ny + 3) / 4, 1);
+    const lbm_params &p = b.h[k].prm;
+    with_storage(b, [&](auto *tag) {
       using T = std::remove_pointer_t<decltype(tag)>;
-      k_ghost_init_c<T><<<g, b, 0, c->stream>>>(L, c->C, c->gidx, (float)c->prm.u_in, (float)c->prm.c_in,
-                                                (float)c->prm.rho_out, (T *)c->fa, (T *)c->fb);
+      k_ghost_init_c<T><<<grd, blk, 0, b.stream>>>(I, b.ns, b.gidx, (float)p.u_in, (float)p.c_in,
+                                                    (float)p.rho_out, (T *)b.fa, (T *)b.fb);
     });
     CK(cudaGetLastError());
   }
-  CK(cudaMemsetAsync(c->acc, 0, 4 * sizeof(double), c->stream));
-  int rc = launch_observables(c);
+  CK(cudaMemsetAsync(b.acc, 0, 4 * sizeof(double) * b.n, b.stream));
+  int rc = launch_observables(b);
   if (rc) return rc;
-  double h[8];
-  CK(cudaMemcpyAsync(h, c->obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  c->mc0 = h[2];
-  c->step = 0;
-  c->have_fields = false;
+  std::vector<double> hobs(8 * (size_t)b.n);
+  CK(cudaMemcpyAsync(hobs.data(), b.obs, hobs.size() * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
+  for (int k = 0; k < b.n; ++k) b.h[k].mc0 = hobs[8 * k + 2];
+  b.step = 0;
   return LBM_OK;
 }
 
-int launch_step(lbm_ctx *c) {
-  const Lattice &L = c->L;
-  const dim3 nb = node_block(), ng = node_grid(L);
-  const int slot = (int)(c->step & 1);
-  prof_begin(c, 0);
-  const unsigned gf = (unsigned)((c->C.nf + 255) / 256);
-  with_storage(c, [&](auto *tag) {
-    using T = std::remove_pointer_t<decltype(tag)>;
-    k_density_c<T><<<gf, 256, 0, c->stream>>>(L, c->C, (const T *)c->fa, c->gidx, c->cnode, c->rhoN);
-  });
-  prof_end(c);
-  if (c->n_bnd > 0) {
-    const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
-    prof_begin(c, 1);
-    k_color_solid<<<gb, 256, 0, c->stream>>>(L, c->bnd_list, c->n_bnd, c->link, c->rhoN);
-    prof_end(c);
+int step_n(Batch &b, int64_t nsteps) {
+  if (nsteps < 0) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const bool use_graph = !b.profiling && !b.debug;
+  if (use_graph && !b.graphs_valid && nsteps > 0) {
+    int rc = build_graphs(b);
+    if (rc) return rc;
   }
-  prof_begin(c, 2);
-  k_normal_c<<<gf, 256, 0, c->stream>>>(L, c->sp, c->C, c->cnode, c->rhoN, c->link, c->ns, c->nrm);
-  prof_end(c);
-  if (c->n_bnd > 0) {
-    const unsigned gb = (unsigned)((c->n_bnd + 255) / 256);
-    prof_begin(c, 3);
-    k_normal_solid<<<gb, 256, 0, c->stream>>>(L, c->bnd_list, c->n_bnd, c->link, c->nrm);
-    prof_end(c);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int parity = (int)(b.step & 1);
+    if (use_graph && b.graphs_valid) {
+      CK(cudaGraphLaunch(b.graph[parity], b.stream));
+    } else {
+      enqueue_step(b, b.stream, b.fa, b.fb, parity, b.profiling);
+      CK(cudaGetLastError());
+    }
+    void *t = b.fa;
+    b.fa = b.fb;
+    b.fb = t;
+    b.step += 1;
   }
-  prof_begin(c, 4);
-  with_storage(c, [&](auto *tag) {
+  return LBM_OK;
+}
+
+int fill_obs(Batch &b, lbm_obs *out, int count) {
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  int rc = launch_observables(b);
+  if (rc) return rc;
+  std::vector<double> hobs(8 * (size_t)b.n), hacc(4 * (size_t)b.n);
+  int derr = 0;
+  CK(cudaMemcpyAsync(hobs.data(), b.obs, hobs.size() * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaMemcpyAsync(hacc.data(), b.acc, hacc.size() * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaMemcpyAsync(&derr, b.err, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
+  if (derr) {
+    b.sticky = LBM_ECUDA;
+    return LBM_ECUDA;
+  }
+  bool bad = false;
+  for (int k = 0; k < count; ++k) {
+    const double *h = &hobs[8 * k], *a = &hacc[4 * k];
+    lbm_obs &o = out[k];
+    std::memset(&o, 0, sizeof(o));
+    o.mass_r = h[0];
+    o.mass_p = h[1];
+    o.mass_c = h[2];
+    o.consumed = a[0];
+    o.rate = b.step > 0 ? a[2 + ((b.step - 1) & 1)] : 0.0;
+    o.gas_saturation = h[3] / (double)b.h[k].n_fluid;
+    o.flux_in = h[4];
+    o.flux_out = h[5];
+    o.n_bad = (int64_t)h[6];
+    o.step = b.step;
+    o.n_fluid = b.h[k].n_fluid;
+    if (b.h[k].d.L.bc_z == 1)
+      o.conversion = o.flux_in != 0.0 ? 1.0 - o.flux_out / o.flux_in : 0.0;
+    else
+      o.conversion = b.h[k].mc0 != 0.0 ? o.consumed / b.h[k].mc0 : 0.0;
+    bad |= o.n_bad != 0;
+  }
+  return bad ? LBM_ENAN : LBM_OK;
+}
+
+// Build a batch: validate, precompute every instance's geometry on the GPU,
+// lay out the slot space, start from equilibrium.
+int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *params, void *stream) {
+  if (n < 1 || n > 65535 || !geoms || !params) return LBM_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    if (check_geometry(&geoms[k]) || check_params(&params[k])) return LBM_EINVAL;
+    if (params[k].storage != params[0].storage) return LBM_EINVAL;
+  }
+  cudaGetDevice(&b.device);
+  b.stream = (cudaStream_t)stream;
+  b.half = params[0].storage == 1;
+  b.n = n;
+  b.h.resize(n);
+  // per-instance node / gidx offsets and static geometry
+  long long nodes = 0, gtot = 0;
+  for (int k = 0; k < n; ++k) {
+    InstHost &ih = b.h[k];
+    ih.prm = params[k];
+    ih.d.L = make_lattice(geoms[k]);
+    ih.d.P = make_step_params(params[k]);
+    ih.d.node_off = (int)nodes;
+    ih.d.gidx_off = (int)gtot;
+    nodes += ih.d.L.n;
+    gtot += ih.d.L.plane * (ih.d.L.nz + 2);
+    if (nodes > (1ll << 31) - 1 || gtot > (1ll << 31) - 1) return LBM_EINVAL;
+  }
+  b.nodes = nodes;
+  int rc = LBM_OK;
+  rc = rc ? rc : dalloc(b, (void **)&b.link, nodes * sizeof(uint32_t));
+  rc = rc ? rc : dalloc(b, (void **)&b.nsv, nodes * sizeof(float4));
+  rc = rc ? rc : dalloc(b, (void **)&b.rhoN, nodes * sizeof(float));
+  rc = rc ? rc : dalloc(b, (void **)&b.nrm, nodes * sizeof(float4));
+  rc = rc ? rc : dalloc(b, (void **)&b.gidx, gtot * sizeof(int));
+  rc = rc ? rc : dalloc(b, (void **)&b.acc, 4 * sizeof(double) * n);
+  rc = rc ? rc : dalloc(b, (void **)&b.acc_scratch, 4 * sizeof(double) * n);
+  rc = rc ? rc : dalloc(b, (void **)&b.obs, 8 * sizeof(double) * n);
+  rc = rc ? rc : dalloc(b, (void **)&b.err, sizeof(int));
+  if (rc) return rc;
+  CK(cudaMemsetAsync(b.rhoN, 0, nodes * sizeof(float), b.stream));
+  CK(cudaMemsetAsync(b.nrm, 0, nodes * sizeof(float4), b.stream));
+  CK(cudaMemsetAsync(b.err, 0, sizeof(int), b.stream));
+  std::vector<uint32_t> hlink(nodes);
+  {
+    // geometry kernels, one instance at a time (one-time set-up)
+    uint8_t *d_solid = nullptr, *d_react = nullptr;
+    long long maxn = 0;
+    for (int k = 0; k < n; ++k) maxn = std::max(maxn, b.h[k].d.L.n);
+    if (cudaMalloc((void **)&d_solid, maxn) != cudaSuccess || cudaMalloc((void **)&d_react, maxn) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaFree(d_solid);
+      cudaFree(d_react);
+      return LBM_ENOMEM;
+    }
+    for (int k = 0; k < n && rc == LBM_OK; ++k) {
+      const Lattice &L = b.h[k].d.L;
+      if (cudaMemcpy(d_solid, geoms[k].solid, L.n, cudaMemcpyHostToDevice) != cudaSuccess ||
+          (geoms[k].reactive && cudaMemcpy(d_react, geoms[k].reactive, L.n, cudaMemcpyHostToDevice) != cudaSuccess)) {
+        rc = LBM_ECUDA;
+        break;
+      }
+      k_geom<<<node_grid(L), node_block(), 0, b.stream>>>(L, d_solid, geoms[k].reactive ? d_react : nullptr,
+                                                          b.link + b.h[k].d.node_off, b.nsv + b.h[k].d.node_off);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(b.stream) != cudaSuccess) rc = LBM_ECUDA;
+    }
+    cudaFree(d_solid);
+    cudaFree(d_react);
+    if (rc) return cuda_fail(b, cudaErrorUnknown);
+    CK(cudaMemcpy(hlink.data(), b.link, nodes * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  }
+  // slot space: per instance its fluid slots in lattice order, then its ghost planes
+  std::vector<uint32_t> hnode, hbnd;
+  std::vector<uint16_t> hkid, hbkid;
+  std::vector<int> hgidx((size_t)gtot, -1);
+  long long s = 0;
+  for (int k = 0; k < n; ++k) {
+    InstHost &ih = b.h[k];
+    const Lattice &L = ih.d.L;
+    const uint32_t *lk = hlink.data() + ih.d.node_off;
+    int *gi = hgidx.data() + ih.d.gidx_off;
+    ih.d.slot_off = (int)s;
+    for (long long i = 0; i < L.n; ++i) {
+      const uint32_t x = (uint32_t)(i % L.nx), y = (uint32_t)((i / L.nx) % L.ny), z = (uint32_t)(i / L.plane);
+      const uint32_t pk = x | (y << 10) | (z << 20);
+      if (lk[i] & BIT_SOLID_BND) {
+        hbnd.push_back(pk);
+        hbkid.push_back((uint16_t)k);
+        ih.n_bnd++;
+      }
+      if (lk[i] & BIT_WALL) ih.n_wall++;
+      if (!(lk[i] & BIT_SOLID)) {
+        gi[i + L.plane] = (int)s;
+        ih.slot_node.push_back((uint32_t)i);
+        hnode.push_back(pk);
+        hkid.push_back((uint16_t)k);
+        ++s;
+      }
+    }
+    ih.d.nf = (int)(s - ih.d.slot_off);
+    ih.n_fluid = ih.d.nf;
+    if (ih.n_fluid == 0) return LBM_EINVAL;
+    ih.d.ghost = (int)s;
+    if (L.bc_z == 1) {
+      for (long long q = 0; q < L.plane; ++q) {
+        gi[q] = (int)(s + q);                                   // inlet plane
+        gi[(L.nz + 1) * L.plane + q] = (int)(s + L.plane + q);  // outlet plane
+      }
+      for (long long q = 0; q < 2 * L.plane; ++q) {
+        hnode.push_back(kNoNode);
+        hkid.push_back((uint16_t)k);
+      }
+      s += 2 * L.plane;
+    }
+    if (s > (1ll << 31) - 1) return LBM_EINVAL;
+  }
+  b.nslots = (int)s;
+  b.ns = (int)((s + 63) / 64 * 64);
+  if ((long long)NPOP * b.ns >= (1ll << 32)) return LBM_EINVAL;   // 32-bit population offsets
+  b.n_bnd = (int)hbnd.size();
+  const size_t elt = b.half ? sizeof(__half) : sizeof(float);
+  const size_t pop_bytes = (size_t)NPOP * b.ns * elt;
+  rc = rc ? rc : dalloc(b, &b.buf0, pop_bytes);
+  rc = rc ? rc : dalloc(b, &b.buf1, pop_bytes);
+  rc = rc ? rc : dalloc(b, (void **)&b.node, hnode.size() * sizeof(uint32_t));
+  rc = rc ? rc : dalloc(b, (void **)&b.inst, n * sizeof(Inst));
+  if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.kid, hkid.size() * sizeof(uint16_t));
+  if (b.n_bnd > 0) {
+    rc = rc ? rc : dalloc(b, (void **)&b.bnd, hbnd.size() * sizeof(uint32_t));
+    if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.bnd_kid, hbkid.size() * sizeof(uint16_t));
+  }
+  if (rc) return rc;
+  std::vector<Inst> hinst(n);
+  for (int k = 0; k < n; ++k) hinst[k] = b.h[k].d;
+  CK(cudaMemsetAsync(b.buf0, 0, pop_bytes, b.stream));
+  CK(cudaMemsetAsync(b.buf1, 0, pop_bytes, b.stream));
+  CK(cudaMemcpy(b.gidx, hgidx.data(), hgidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b.node, hnode.data(), hnode.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b.inst, hinst.data(), n * sizeof(Inst), cudaMemcpyHostToDevice));
+  if (b.kid) CK(cudaMemcpy(b.kid, hkid.data(), hkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  if (b.bnd) CK(cudaMemcpy(b.bnd, hbnd.data(), hbnd.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  if (b.bnd_kid) CK(cudaMemcpy(b.bnd_kid, hbkid.data(), hbkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  b.fa = b.buf0;
+  b.fb = b.buf1;
+  for (int k = 0; k < n; ++k) {
+    const Inst &I = b.h[k].d;
+    with_storage(b, [&](auto *tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      k_init_c<T><<<(I.nf + 255) / 256, 256, 0, b.stream>>>(I, b.ns, b.node, nullptr, nullptr, nullptr, nullptr, 1.0f,
+                                                            0.0f, (float)b.h[k].prm.c_init, (T *)b.fa, (T *)b.fb);
+    });
+    CK(cudaGetLastError());
+  }
+  return reset_after_state(b);
+}
+
+// Before one instance's state is replaced: make buf0 hold every instance's
+// current state (and buf1 too), so the step parity can restart at 0.
+int normalise_buffers(Batch &b) {
+  const size_t pop_bytes = (size_t)NPOP * b.ns * (b.half ? sizeof(__half) : sizeof(float));
+  if (b.fa != b.buf0) CK(cudaMemcpyAsync(b.buf0, b.buf1, pop_bytes, cudaMemcpyDeviceToDevice, b.stream));
+  CK(cudaMemcpyAsync(b.buf1, b.buf0, pop_bytes, cudaMemcpyDeviceToDevice, b.stream));
+  b.fa = b.buf0;
+  b.fb = b.buf1;
+  return LBM_OK;
+}
+
+int init_fields(Batch &b, int k, const float *rho_r, const float *rho_p, const float *conc, const float *u) {
+  if (!rho_r || !rho_p || !conc || k < 0 || k >= b.n) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const Inst &I = b.h[k].d;
+  const size_t nb = (size_t)I.L.n * sizeof(float);
+  float *d = nullptr;
+  if (cudaMalloc((void **)&d, nb * (u ? 6 : 3)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  int rc = LBM_OK;
+  if (cudaMemcpy(d, rho_r, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy((char *)d + nb, rho_p, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy((char *)d + 2 * nb, conc, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (u && cudaMemcpy((char *)d + 3 * nb, u, 3 * nb, cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = cuda_fail(b, cudaErrorUnknown);
+  if (!rc) rc = normalise_buffers(b);
+  if (!rc) {
+    const float *fd = d;
+    with_storage(b, [&](auto *tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      k_init_c<T><<<(I.nf + 255) / 256, 256, 0, b.stream>>>(I, b.ns, b.node, fd, fd + I.L.n, fd + 2 * I.L.n,
+                                                            u ? fd + 3 * I.L.n : nullptr, 0.f, 0.f, 0.f,
+                                                            (T *)b.fa, (T *)b.fb);
+    });
+    if (cudaGetLastError() != cudaSuccess) rc = cuda_fail(b, cudaErrorLaunchFailure);
+  }
+  if (!rc) rc = reset_after_state(b);
+  cudaStreamSynchronize(b.stream);
+  cudaFree(d);
+  return rc;
+}
+
+int get_state(Batch &b, int k, float *dst, size_t bytes) {
+  if (!dst || k < 0 || k >= b.n) return LBM_EINVAL;
+  const InstHost &ih = b.h[k];
+  if (bytes != (size_t)NPOP * ih.d.L.n * sizeof(float)) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const size_t nf = (size_t)ih.d.nf;
+  float *d = nullptr;
+  if (cudaMalloc((void **)&d, (size_t)NPOP * nf * sizeof(float)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  with_storage(b, [&](auto *tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
-    k_main_c<T><<<(unsigned)((c->C.nf + CGLBM_MAIN_BLOCK - 1) / CGLBM_MAIN_BLOCK), CGLBM_MAIN_BLOCK, 0,
-                  c->stream>>>(L, c->C, c->sp, (const T *)c->fa, (T *)c->fb, c->gidx, c->cnode, c->link, c->nrm,
-                               c->acc, slot, c->debug ? c->dbg_H : nullptr, c->debug ? c->dbg_delta : nullptr);
+    k_slots_to_f32<T><<<(unsigned)((nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, (const T *)b.fa, d);
   });
-  prof_end(c);
+  std::vector<float> h((size_t)NPOP * nf);
+  cudaError_t e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(float), cudaMemcpyDeviceToHost, b.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b.stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(b, e);
+  std::memset(dst, 0, bytes);   // solid nodes hold no populations
+  const long long n = ih.d.L.n;
+  for (int p = 0; p < NPOP; ++p) {
+    float *o = dst + (size_t)p * n;
+    const float *s = h.data() + (size_t)p * nf;
+    for (size_t t = 0; t < nf; ++t) o[ih.slot_node[t]] = s[t];
+  }
+  return LBM_OK;
+}
+
+int set_state(Batch &b, int k, const float *src, size_t bytes) {
+  if (!src || k < 0 || k >= b.n) return LBM_EINVAL;
+  const InstHost &ih = b.h[k];
+  if (bytes != (size_t)NPOP * ih.d.L.n * sizeof(float)) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const size_t nf = (size_t)ih.d.nf;
+  const long long n = ih.d.L.n;
+  std::vector<float> h((size_t)NPOP * nf);
+  for (int p = 0; p < NPOP; ++p) {
+    const float *s = src + (size_t)p * n;
+    float *o = h.data() + (size_t)p * nf;
+    for (size_t t = 0; t < nf; ++t) o[t] = s[ih.slot_node[t]];
+  }
+  float *d = nullptr;
+  if (cudaMalloc((void **)&d, h.size() * sizeof(float)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, b.stream);
+  if (e == cudaSuccess && normalise_buffers(b) != LBM_OK) e = cudaErrorUnknown;
+  if (e == cudaSuccess) {
+    with_storage(b, [&](auto *tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      k_f32_to_slots<T><<<(unsigned)((nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, d, (T *)b.fa, (T *)b.fb);
+    });
+    e = cudaStreamSynchronize(b.stream);
+  }
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(b, e);
+  return reset_after_state(b);
+}
+
+// time each launch shape of the tunable kernels on the current state (the
+// candidate launches write only the output buffer, the per-node fields and a
+// scratch accumulator, which the next step recomputes) and keep the fastest
+int tune(Batch &b, int32_t *chosen) {
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int reps = 5;
+  auto time_it = [&](auto &&launch) {
+    launch();
+    cudaEventRecord(e0, b.stream);
+    for (int r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, b.stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  const int cand_main[3] = {64, 128, 256}, cand_other[3] = {128, 256, 512};
+  float best = 1e30f;
+  int pick = b.main_block;
+  for (int c : cand_main) {
+    b.main_block = c;
+    const float t = time_it([&] {
+      with_storage(b, [&](auto *tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        launch_main<T>(b, b.stream, b.fa, b.fb, b.acc_scratch, 0);
+      });
+    });
+    if (t < best) {
+      best = t;
+      pick = c;
+    }
+  }
+  b.main_block = pick;
+  best = 1e30f;
+  pick = b.dens_block;
+  for (int c : cand_other) {
+    b.dens_block = c;
+    const float t = time_it([&] {
+      with_storage(b, [&](auto *tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        launch_density<T>(b, b.stream, b.fa);
+      });
+    });
+    if (t < best) {
+      best = t;
+      pick = c;
+    }
+  }
+  b.dens_block = pick;
+  best = 1e30f;
+  pick = b.norm_block;
+  for (int c : cand_other) {
+    b.norm_block = c;
+    const float t = time_it([&] { launch_normal(b, b.stream); });
+    if (t < best) {
+      best = t;
+      pick = c;
+    }
+  }
+  b.norm_block = pick;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   CK(cudaGetLastError());
-  void *t = c->fa;
-  c->fa = c->fb;
-  c->fb = t;
-  c->step += 1;
-  c->have_fields = true;
+  // the fields touched by the candidates are recomputed by the next step from fa
+  drop_graphs(b);
+  if (chosen) {
+    chosen[0] = b.main_block;
+    chosen[1] = b.dens_block;
+    chosen[2] = b.norm_block;
+  }
+  return LBM_OK;
+}
+
+int get_field(Batch &b, int k, int32_t which, float *dst, size_t bytes) {
+  if (!dst || k < 0 || k >= b.n) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const InstHost &ih = b.h[k];
+  const size_t n = (size_t)ih.d.L.n;
+  const size_t one = n * sizeof(float);
+  const size_t off = (size_t)ih.d.node_off;
+  if (which == LBM_FIELD_RHON || which == LBM_FIELD_GRADMAG || which == LBM_FIELD_NN || which == LBM_FIELD_CURV ||
+      which == LBM_FIELD_DELTA) {
+    if (bytes != one) return LBM_EINVAL;
+  } else if (which == LBM_FIELD_NORMAL || which == LBM_FIELD_NS) {
+    if (bytes != 3 * one) return LBM_EINVAL;
+  } else {
+    return LBM_EINVAL;
+  }
+  CK(cudaStreamSynchronize(b.stream));
+  if (which == LBM_FIELD_RHON) {
+    CK(cudaMemcpy(dst, b.rhoN + off, one, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+  }
+  if (which == LBM_FIELD_CURV || which == LBM_FIELD_DELTA) {
+    if (!b.dbg_H) return LBM_EINVAL;
+    CK(cudaMemcpy(dst, (which == LBM_FIELD_CURV ? b.dbg_H : b.dbg_delta) + off, one, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+  }
+  if (which == LBM_FIELD_NN) {
+    std::vector<uint32_t> hv(n);
+    CK(cudaMemcpy(hv.data(), b.link + off, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) dst[i] = (hv[i] & BIT_SOLID) ? 0.f : (float)((hv[i] >> NN_SHIFT) & 7u);
+    return LBM_OK;
+  }
+  std::vector<float4> hv(n);
+  CK(cudaMemcpy(hv.data(), (which == LBM_FIELD_NS ? b.nsv : b.nrm) + off, n * sizeof(float4), cudaMemcpyDeviceToHost));
+  if (which == LBM_FIELD_GRADMAG) {
+    for (size_t i = 0; i < n; ++i) dst[i] = hv[i].w;
+    return LBM_OK;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    dst[i] = hv[i].x;
+    dst[n + i] = hv[i].y;
+    dst[2 * n + i] = hv[i].z;
+  }
+  return LBM_OK;
+}
+
+int set_debug(Batch &b, int32_t enable) {
+  cudaSetDevice(b.device);
+  if (enable && !b.dbg_H) {
+    const size_t nb = (size_t)b.nodes * sizeof(float);
+    if (dalloc(b, (void **)&b.dbg_H, nb) || dalloc(b, (void **)&b.dbg_delta, nb)) return LBM_ENOMEM;
+    CK(cudaMemset(b.dbg_H, 0, nb));
+    CK(cudaMemset(b.dbg_delta, 0, nb));
+  }
+  b.debug = enable != 0;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+int profile(Batch &b, int32_t max_launches) {
+  if (max_launches < 0) return LBM_EINVAL;
+  cudaSetDevice(b.device);
+  const size_t need = (size_t)max_launches * 2;
+  while (b.ev.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    b.ev.push_back(e);
+  }
+  b.ev_kind.assign(b.ev.size() / 2 + 1, 0);
+  b.ev_used = 0;
+  b.profiling = max_launches > 0;
+  return LBM_OK;
+}
+
+int profile_read(Batch &b, double *ms, int64_t *launches, int32_t n) {
+  if (!ms || !launches || n < 1 || n > LBM_NKERNELS) return LBM_EINVAL;
+  cudaSetDevice(b.device);
+  CK(cudaStreamSynchronize(b.stream));
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i + 1 < b.ev_used; i += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, b.ev[i], b.ev[i + 1]));
+    const int k = b.ev_kind[i / 2];
+    if (k < n) {
+      ms[k] += t;
+      launches[k] += 1;
+    }
+  }
   return LBM_OK;
 }
 
@@ -336,388 +939,128 @@ const char *lbm_strerror(int code) {
 }
 
 int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out) {
-  if (!geom || !params || !out || !geom->solid) return LBM_EINVAL;
-  if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return LBM_EINVAL;
-  if (geom->bc_z != 0 && geom->bc_z != 1) return LBM_EINVAL;
-  if (geom->bc_z == 1 && geom->nz < 2) return LBM_EINVAL;
-  // packed slot coordinates (10 + 10 + 11 bits)
-  if (geom->nx > 1024 || geom->ny > 1024 || geom->nz > 2048) return LBM_EINVAL;
-  int rc = check_params(params);
-  if (rc) return rc;
-  const long long n = (long long)geom->nx * geom->ny * geom->nz;
-  if (n > (1ll << 31) - 1) return LBM_EINVAL;   // node lists are 32-bit
-  // 32-bit population offsets: 45 populations x (nz + 2) planes must stay below 2^32
-  if ((long long)NPOP * geom->nx * geom->ny * (geom->nz + 2) >= (1ll << 32)) return LBM_EINVAL;
+  if (!out || check_geometry(geom) || check_params(params)) return LBM_EINVAL;
   long long nfl = 0;
+  const long long n = (long long)geom->nx * geom->ny * geom->nz;
   for (long long i = 0; i < n; ++i) nfl += geom->solid[i] ? 0 : 1;
   if (nfl == 0) return LBM_EINVAL;
-
   lbm_ctx *c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ENOMEM;
-  cudaGetDevice(&c->device);
-  c->prm = *params;
-  c->stream = (cudaStream_t)params->cuda_stream;
-  Lattice &L = c->L;
-  L.nx = geom->nx;
-  L.ny = geom->ny;
-  L.nz = geom->nz;
-  L.bc_z = geom->bc_z;
-  L.n = n;
-  L.plane = (long long)L.nx * L.ny;
-  L.pstride = L.plane * (L.nz + 2);
-  c->n_fluid = nfl;
-  fill_step_params(c);
-
-
-  uint8_t *d_solid = nullptr, *d_react = nullptr;
-  rc = LBM_OK;
-  rc = rc ? rc : dalloc(c, (void **)&c->link, n * sizeof(uint32_t));
-  rc = rc ? rc : dalloc(c, (void **)&c->ns, n * sizeof(float4));
-  rc = rc ? rc : dalloc(c, (void **)&c->rhoN, n * sizeof(float));
-  rc = rc ? rc : dalloc(c, (void **)&c->nrm, n * sizeof(float4));
-  rc = rc ? rc : dalloc(c, (void **)&c->acc, 8 * sizeof(double));
-  rc = rc ? rc : dalloc(c, (void **)&c->obs, 8 * sizeof(double));
-  rc = rc ? rc : dalloc(c, (void **)&c->err, sizeof(int));
-  if (!rc && cudaMalloc((void **)&d_solid, n) != cudaSuccess) rc = LBM_ENOMEM;
-  if (!rc && geom->reactive && cudaMalloc((void **)&d_react, n) != cudaSuccess) rc = LBM_ENOMEM;
+  const int rc = batch_create(c->b, 1, geom, params, params->cuda_stream);
   if (rc) {
-    (void)cudaGetLastError();
-    cudaFree(d_solid);
-    cudaFree(d_react);
-    free_all(c);
+    free_all(c->b);
     delete c;
     return rc;
   }
-  auto fail = [&](int code) {
-    cudaFree(d_solid);
-    cudaFree(d_react);
-    free_all(c);
-    delete c;
-    return code;
-  };
-  if (cudaMemcpy(d_solid, geom->solid, n, cudaMemcpyHostToDevice) != cudaSuccess) return fail(LBM_ECUDA);
-  if (d_react && cudaMemcpy(d_react, geom->reactive, n, cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail(LBM_ECUDA);
-  if (cudaMemsetAsync(c->rhoN, 0, n * sizeof(float), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
-  if (cudaMemsetAsync(c->nrm, 0, n * sizeof(float4), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
-  if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) return fail(LBM_ECUDA);
-  k_geom<<<node_grid(L), node_block(), 0, c->stream>>>(L, d_solid, d_react, c->link, c->ns);
-  if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
-  // boundary-solid list, built from the device flags in node order
-  std::vector<uint32_t> hlink(n);
-  if (cudaMemcpyAsync(hlink.data(), c->link, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess)
-    return fail(LBM_ECUDA);
-  cudaFree(d_solid);
-  cudaFree(d_react);
-  d_solid = d_react = nullptr;
-  // boundary-solid list, compact slots (fluid nodes in lattice order, then the
-  // inlet and outlet ghost planes in column mode) and the position -> slot map
-  std::vector<uint32_t> blist, cnode;
-  std::vector<int> gidx((size_t)L.plane * (L.nz + 2), -1);
-  for (long long i = 0; i < n; ++i) {
-    const uint32_t x = (uint32_t)(i % L.nx), y = (uint32_t)((i / L.nx) % L.ny), z = (uint32_t)(i / L.plane);
-    if (hlink[i] & BIT_SOLID_BND) blist.push_back(x | (y << 10) | (z << 20));
-    if (hlink[i] & BIT_WALL) c->n_wall++;
-    if (!(hlink[i] & BIT_SOLID)) {
-      gidx[(size_t)(i + L.plane)] = (int)cnode.size();
-      c->h_slot_node.push_back((uint32_t)i);
-      cnode.push_back(x | (y << 10) | (z << 20));
-    }
-  }
-  c->C.nf = (int)cnode.size();
-  const long long nghost = L.bc_z == 1 ? 2 * L.plane : 0;
-  c->C.ns = (int)((c->C.nf + nghost + 63) / 64 * 64);
-  if (L.bc_z == 1)
-    for (long long q = 0; q < L.plane; ++q) {
-      gidx[(size_t)q] = c->C.nf + (int)q;                                         // inlet plane
-      gidx[(size_t)((L.nz + 1) * L.plane + q)] = c->C.nf + (int)(L.plane + q);    // outlet plane
-    }
-  c->half = params->storage == 1;
-  const size_t pop_bytes = (size_t)NPOP * c->C.ns * (c->half ? sizeof(__half) : sizeof(float));
-  if (dalloc(c, (void **)&c->fa, pop_bytes) || dalloc(c, (void **)&c->fb, pop_bytes) ||
-      dalloc(c, (void **)&c->gidx, gidx.size() * sizeof(int)) ||
-      dalloc(c, (void **)&c->cnode, cnode.size() * sizeof(uint32_t)))
-    return fail(LBM_ENOMEM);
-  if (cudaMemsetAsync(c->fa, 0, pop_bytes, c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->fb, 0, pop_bytes, c->stream) != cudaSuccess ||
-      cudaMemcpy(c->gidx, gidx.data(), gidx.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->cnode, cnode.data(), cnode.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail(LBM_ECUDA);
-  c->n_bnd = (long long)blist.size();
-  if (c->n_bnd > 0) {
-    if (dalloc(c, (void **)&c->bnd_list, blist.size() * sizeof(uint32_t))) return fail(LBM_ENOMEM);
-    if (cudaMemcpy(c->bnd_list, blist.data(), blist.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
-      return fail(LBM_ECUDA);
-  }
-  with_storage(c, [&](auto *tag) {
-    using T = std::remove_pointer_t<decltype(tag)>;
-    k_init_c<T><<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
-        L, c->C, c->cnode, nullptr, nullptr, nullptr, nullptr, 1.0f, 0.0f, (float)params->c_init, (T *)c->fa,
-        (T *)c->fb);
-  });
-  if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA);
-  rc = reset_after_state(c);
-  if (rc) return fail(rc);
   *out = c;
   return LBM_OK;
 }
 
-int lbm_step(lbm_ctx *c, int64_t nsteps) {
-  if (!c || nsteps < 0) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
-  for (int64_t s = 0; s < nsteps; ++s) {
-    int rc = launch_step(c);
-    if (rc) return rc;
-  }
-  return LBM_OK;
-}
+int lbm_step(lbm_ctx *c, int64_t nsteps) { return c ? step_n(c->b, nsteps) : LBM_EINVAL; }
 
 int lbm_observables(lbm_ctx *c, lbm_obs *out) {
   if (!c || !out) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
-  int rc = launch_observables(c);
-  if (rc) return rc;
-  double h[8], a[4];
-  int derr = 0;
-  CK(cudaMemcpyAsync(h, c->obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(&derr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (derr) {
-    c->sticky = LBM_ECUDA;
-    return LBM_ECUDA;
-  }
-  std::memset(out, 0, sizeof(*out));
-  out->mass_r = h[0];
-  out->mass_p = h[1];
-  out->mass_c = h[2];
-  out->consumed = a[0];
-  out->rate = c->step > 0 ? a[2 + ((c->step - 1) & 1)] : 0.0;
-  out->gas_saturation = h[3] / (double)c->n_fluid;
-  out->flux_in = h[4];
-  out->flux_out = h[5];
-  out->n_bad = (int64_t)h[6];
-  out->step = c->step;
-  out->n_fluid = c->n_fluid;
-  if (c->L.bc_z == 1)
-    out->conversion = out->flux_in != 0.0 ? 1.0 - out->flux_out / out->flux_in : 0.0;
-  else
-    out->conversion = c->mc0 != 0.0 ? out->consumed / c->mc0 : 0.0;
-  return out->n_bad ? LBM_ENAN : LBM_OK;
+  return fill_obs(c->b, out, 1);
 }
 
 int lbm_reaction(lbm_ctx *c, double *rate, double *consumed) {
   if (!c) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
+  Batch &b = c->b;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
   double a[4];
-  CK(cudaMemcpyAsync(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (rate) *rate = c->step > 0 ? a[2 + ((c->step - 1) & 1)] : 0.0;
+  CK(cudaMemcpyAsync(a, b.acc, sizeof(a), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
+  if (rate) *rate = b.step > 0 ? a[2 + ((b.step - 1) & 1)] : 0.0;
   if (consumed) *consumed = a[0];
   return LBM_OK;
 }
 
 int lbm_init_fields(lbm_ctx *c, const float *rho_r, const float *rho_p, const float *conc, const float *u) {
-  if (!c || !rho_r || !rho_p || !conc) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
-  const Lattice &L = c->L;
-  const size_t nb = (size_t)L.n * sizeof(float);
-  float *d = nullptr;
-  const size_t tot = nb * (u ? 6 : 3);
-  if (cudaMalloc((void **)&d, tot) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return LBM_ENOMEM;
-  }
-  int rc = LBM_OK;
-  if (cudaMemcpy(d, rho_r, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy((char *)d + nb, rho_p, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy((char *)d + 2 * nb, conc, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
-      (u && cudaMemcpy((char *)d + 3 * nb, u, 3 * nb, cudaMemcpyHostToDevice) != cudaSuccess))
-    rc = cuda_fail(c, cudaErrorUnknown);
-  if (!rc) {
-    const float *fd = d;
-    with_storage(c, [&](auto *tag) {
-      using T = std::remove_pointer_t<decltype(tag)>;
-      k_init_c<T><<<(unsigned)((c->C.nf + 255) / 256), 256, 0, c->stream>>>(
-          L, c->C, c->cnode, fd, fd + L.n, fd + 2 * L.n, u ? fd + 3 * L.n : nullptr, 0.f, 0.f, 0.f, (T *)c->fa,
-          (T *)c->fb);
-    });
-    if (cudaGetLastError() != cudaSuccess) rc = cuda_fail(c, cudaErrorLaunchFailure);
-  }
-  if (!rc) rc = reset_after_state(c);
-  cudaStreamSynchronize(c->stream);
-  cudaFree(d);
-  return rc;
+  return c ? init_fields(c->b, 0, rho_r, rho_p, conc, u) : LBM_EINVAL;
 }
 
-int lbm_get_state(lbm_ctx *c, float *dst, size_t bytes) {
-  if (!c || !dst) return LBM_EINVAL;
-  const Lattice &L = c->L;
-  if (bytes != (size_t)NPOP * L.n * sizeof(float)) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
-  const size_t nf = (size_t)c->C.nf;
-  float *d = nullptr;
-  if (cudaMalloc((void **)&d, (size_t)NPOP * nf * sizeof(float)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return LBM_ENOMEM;
-  }
-  with_storage(c, [&](auto *tag) {
-    using T = std::remove_pointer_t<decltype(tag)>;
-    k_slots_to_f32<T><<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(c->C, (const T *)c->fa, d);
-  });
-  std::vector<float> h((size_t)NPOP * nf);
-  cudaError_t e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(d);
-  if (e != cudaSuccess) return cuda_fail(c, e);
-  std::memset(dst, 0, bytes);   // solid nodes hold no populations
-  for (int p = 0; p < NPOP; ++p) {
-    float *o = dst + (size_t)p * L.n;
-    const float *s = h.data() + (size_t)p * nf;
-    for (size_t t = 0; t < nf; ++t) o[c->h_slot_node[t]] = s[t];
-  }
-  return LBM_OK;
-}
+int lbm_get_state(lbm_ctx *c, float *dst, size_t bytes) { return c ? get_state(c->b, 0, dst, bytes) : LBM_EINVAL; }
 
 int lbm_set_state(lbm_ctx *c, const float *src, size_t bytes) {
-  if (!c || !src) return LBM_EINVAL;
-  const Lattice &L = c->L;
-  if (bytes != (size_t)NPOP * L.n * sizeof(float)) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
-  const size_t nf = (size_t)c->C.nf;
-  std::vector<float> h((size_t)NPOP * nf);
-  for (int p = 0; p < NPOP; ++p) {
-    const float *s = src + (size_t)p * L.n;
-    float *o = h.data() + (size_t)p * nf;
-    for (size_t t = 0; t < nf; ++t) o[t] = s[c->h_slot_node[t]];
-  }
-  float *d = nullptr;
-  if (cudaMalloc((void **)&d, h.size() * sizeof(float)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return LBM_ENOMEM;
-  }
-  cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) {
-    with_storage(c, [&](auto *tag) {
-      using T = std::remove_pointer_t<decltype(tag)>;
-      k_f32_to_slots<T><<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(c->C, d, (T *)c->fa, (T *)c->fb);
-    });
-    e = cudaStreamSynchronize(c->stream);
-  }
-  cudaFree(d);
-  if (e != cudaSuccess) return cuda_fail(c, e);
-  return reset_after_state(c);
+  return c ? set_state(c->b, 0, src, bytes) : LBM_EINVAL;
 }
 
-int lbm_set_debug(lbm_ctx *c, int32_t enable) {
-  if (!c) return LBM_EINVAL;
-  cudaSetDevice(c->device);
-  if (enable && !c->dbg_H) {
-    const size_t nb = (size_t)c->L.n * sizeof(float);
-    if (dalloc(c, (void **)&c->dbg_H, nb) || dalloc(c, (void **)&c->dbg_delta, nb)) return LBM_ENOMEM;
-    if (cudaMemset(c->dbg_H, 0, nb) != cudaSuccess || cudaMemset(c->dbg_delta, 0, nb) != cudaSuccess)
-      return cuda_fail(c, cudaErrorUnknown);
-  }
-  c->debug = enable != 0;
-  return LBM_OK;
-}
+int lbm_set_debug(lbm_ctx *c, int32_t enable) { return c ? set_debug(c->b, enable) : LBM_EINVAL; }
 
 int lbm_get_field(lbm_ctx *c, int32_t which, float *dst, size_t bytes) {
-  if (!c || !dst) return LBM_EINVAL;
-  if (c->sticky) return c->sticky;
-  cudaSetDevice(c->device);
-  const Lattice &L = c->L;
-  const size_t n = (size_t)L.n;
-  const size_t one = n * sizeof(float);
-  if (which == LBM_FIELD_RHON || which == LBM_FIELD_GRADMAG || which == LBM_FIELD_NN ||
-      which == LBM_FIELD_CURV || which == LBM_FIELD_DELTA) {
-    if (bytes != one) return LBM_EINVAL;
-  } else if (which == LBM_FIELD_NORMAL || which == LBM_FIELD_NS) {
-    if (bytes != 3 * one) return LBM_EINVAL;
-  } else {
-    return LBM_EINVAL;
-  }
-  CK(cudaStreamSynchronize(c->stream));
-  if (which == LBM_FIELD_RHON) {
-    CK(cudaMemcpy(dst, c->rhoN, one, cudaMemcpyDeviceToHost));
-    return LBM_OK;
-  }
-  if (which == LBM_FIELD_CURV || which == LBM_FIELD_DELTA) {
-    if (!c->dbg_H) return LBM_EINVAL;
-    CK(cudaMemcpy(dst, which == LBM_FIELD_CURV ? c->dbg_H : c->dbg_delta, one, cudaMemcpyDeviceToHost));
-    return LBM_OK;
-  }
-  if (which == LBM_FIELD_NN) {
-    std::vector<uint32_t> h(n);
-    CK(cudaMemcpy(h.data(), c->link, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < n; ++i) dst[i] = (float)((h[i] >> NN_SHIFT) & 7u);
-    return LBM_OK;
-  }
-  std::vector<float4> h(n);
-  CK(cudaMemcpy(h.data(), which == LBM_FIELD_NS ? c->ns : c->nrm, n * sizeof(float4), cudaMemcpyDeviceToHost));
-  if (which == LBM_FIELD_GRADMAG) {
-    for (size_t i = 0; i < n; ++i) dst[i] = h[i].w;
-    return LBM_OK;
-  }
-  for (size_t i = 0; i < n; ++i) {
-    dst[i] = h[i].x;
-    dst[n + i] = h[i].y;
-    dst[2 * n + i] = h[i].z;
-  }
-  return LBM_OK;
+  return c ? get_field(c->b, 0, which, dst, bytes) : LBM_EINVAL;
 }
 
-int lbm_profile(lbm_ctx *c, int32_t max_launches) {
-  if (!c || max_launches < 0) return LBM_EINVAL;
-  cudaSetDevice(c->device);
-  const size_t need = (size_t)max_launches * 2;
-  while (c->ev.size() < need) {
-    cudaEvent_t e;
-    CK(cudaEventCreate(&e));
-    c->ev.push_back(e);
-  }
-  c->ev_kind.assign(c->ev.size() / 2 + 1, 0);
-  c->ev_used = 0;
-  c->profiling = max_launches > 0;
-  return LBM_OK;
-}
+int lbm_profile(lbm_ctx *c, int32_t max_launches) { return c ? profile(c->b, max_launches) : LBM_EINVAL; }
 
 int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches, int32_t n) {
-  if (!c || !ms || !launches || n < 1 || n > LBM_NKERNELS) return LBM_EINVAL;
-  cudaSetDevice(c->device);
-  CK(cudaStreamSynchronize(c->stream));
-  for (int k = 0; k < n; ++k) {
-    ms[k] = 0.0;
-    launches[k] = 0;
-  }
-  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
-    const int k = c->ev_kind[i / 2];
-    if (k < n) {
-      ms[k] += t;
-      launches[k] += 1;
-    }
-  }
-  return LBM_OK;
+  return c ? profile_read(c->b, ms, launches, n) : LBM_EINVAL;
 }
+
+int lbm_tune(lbm_ctx *c, int32_t *blocks) { return c ? tune(c->b, blocks) : LBM_EINVAL; }
 
 int lbm_info(lbm_ctx *c, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd, int64_t *device_bytes) {
   if (!c) return LBM_EINVAL;
-  if (n_fluid) *n_fluid = c->n_fluid;
-  if (n_wall) *n_wall = c->n_wall;
-  if (n_solid_bnd) *n_solid_bnd = c->n_bnd;
-  if (device_bytes) *device_bytes = (int64_t)c->device_bytes;
+  if (n_fluid) *n_fluid = c->b.h[0].n_fluid;
+  if (n_wall) *n_wall = c->b.h[0].n_wall;
+  if (n_solid_bnd) *n_solid_bnd = c->b.h[0].n_bnd;
+  if (device_bytes) *device_bytes = (int64_t)c->b.device_bytes;
   return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->b.device);
+  cudaStreamSynchronize(c->b.stream);
+  free_all(c->b);
+  delete c;
+}
+
+int lbm_batch_create(int32_t n, const lbm_geometry *geoms, const lbm_params *params, void *cuda_stream,
+                     lbm_batch **out) {
+  if (!out || n < 1 || !geoms || !params) return LBM_EINVAL;
+  lbm_batch *bt = new (std::nothrow) lbm_batch();
+  if (!bt) return LBM_ENOMEM;
+  const int rc = batch_create(bt->b, n, geoms, params, cuda_stream);
+  if (rc) {
+    free_all(bt->b);
+    delete bt;
+    return rc;
+  }
+  *out = bt;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *bt, int64_t nsteps) { return bt ? step_n(bt->b, nsteps) : LBM_EINVAL; }
+
+int lbm_batch_observables(lbm_batch *bt, lbm_obs *out, int32_t count) {
+  if (!bt || !out || count != bt->b.n) return LBM_EINVAL;
+  return fill_obs(bt->b, out, count);
+}
+
+int lbm_batch_get_state(lbm_batch *bt, int32_t k, float *dst, size_t bytes) {
+  return bt ? get_state(bt->b, k, dst, bytes) : LBM_EINVAL;
+}
+
+int lbm_batch_set_state(lbm_batch *bt, int32_t k, const float *src, size_t bytes) {
+  return bt ? set_state(bt->b, k, src, bytes) : LBM_EINVAL;
+}
+
+int lbm_batch_tune(lbm_batch *bt, int32_t *blocks) { return bt ? tune(bt->b, blocks) : LBM_EINVAL; }
+
+int lbm_batch_profile(lbm_batch *bt, int32_t max_launches) { return bt ? profile(bt->b, max_launches) : LBM_EINVAL; }
+
+int lbm_batch_profile_read(lbm_batch *bt, double *ms, int64_t *launches, int32_t n) {
+  return bt ? profile_read(bt->b, ms, launches, n) : LBM_EINVAL;
+}
+
+void lbm_batch_destroy(lbm_batch *bt) {
+  if (!bt) return;
+  cudaSetDevice(bt->b.device);
+  cudaStreamSynchronize(bt->b.stream);
+  free_all(bt->b);
+  delete bt;
 }
 
 int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, const uint8_t *reactive,
@@ -752,9 +1095,7 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   L.n = n;
   L.plane = (long long)nx * ny;
   L.pstride = n;
-  lbm_ctx tmp;                      // parameter conversion only; owns no memory
-  tmp.prm = *params;
-  fill_step_params(&tmp);
+  const StepParams sp = make_step_params(*params);
   const float *fin = f_in - L.plane;
   float *fout = f_out - L.plane;
   const dim3 nb = node_block(), ng = node_grid(L);
@@ -762,9 +1103,9 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   k_geom<<<ng, nb, 0, st>>>(L, solid, reactive, link, ns);
   k_density<<<ng, nb, 0, st>>>(L, fin, link, rhoN);
   k_color_solid_all<<<ng, nb, 0, st>>>(L, link, rhoN);
-  k_normal<<<ng, nb, 0, st>>>(L, tmp.sp, rhoN, link, ns, nrm);
+  k_normal<<<ng, nb, 0, st>>>(L, sp, rhoN, link, ns, nrm);
   k_normal_solid_all<<<ng, nb, 0, st>>>(L, link, nrm);
-  k_main<<<ng, nb, 0, st>>>(L, tmp.sp, fin, fout, link, nrm, acc, 0, nullptr, nullptr);
+  k_main<<<ng, nb, 0, st>>>(L, sp, fin, fout, link, nrm, acc, 0, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
   if (delta_sum &&
       cudaMemcpyAsync(delta_sum, acc + 2, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -772,12 +1113,5 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   return LBM_OK;
 }
 
-void lbm_destroy(lbm_ctx *c) {
-  if (!c) return;
-  cudaSetDevice(c->device);
-  cudaStreamSynchronize(c->stream);
-  free_all(c);
-  delete c;
-}
 
 }  // extern "C"

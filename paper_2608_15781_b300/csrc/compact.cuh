@@ -1,41 +1,62 @@
-// Compact population layout: only fluid nodes (and the column ghost planes) own
-// population slots.
+// Compact, batched population layout and the per-step kernels that use it.
 //
-// In the paper's bicontinuous supports about half the lattice is solid.  A
-// dense structure-of-arrays layout moves the solid nodes' slots with every
-// 32-byte sector that also holds fluid data, and the fluid-only stores leave
-// sectors partly written, which the memory system completes with an extra
-// read.  Here population p of slot s sits at f[p * ns + s]; slots 0 .. nf-1 are
-// the fluid nodes in lattice order, slots nf .. nf + 2 * plane - 1 the inlet and
-// outlet ghost planes (column mode).  gidx maps every stored lattice position
-// (plane z + 1 in [0, nz + 1]) to its slot, or -1 for a solid node.  Fields
-// that stencils read (rho^N, n, link words, n_s) stay dense, indexed by node.
+// Only fluid nodes (and the column ghost planes) own population slots.  In the
+// paper's bicontinuous supports about half the lattice is solid; a dense
+// structure-of-arrays layout moves the solid nodes' slots with every 32-byte
+// sector that also holds fluid data, and fluid-only stores leave sectors partly
+// written, which the memory system completes with an extra read.
 //
-// Storage type T: float (FP32 values) or __half (FP16 deviations from fixed
-// reference equilibria: f^r_i - w_i, f^p_i, g_j - w_j, i.e. reactant liquid at
-// rest with C = 1; all arithmetic in FP32).
+// A batch holds one or more independent lattices ("instances", each with its
+// own size, mask and parameters).  All their slots share one slot space:
+// instance k owns the fluid slots [slot_off, slot_off + nf) in lattice order and,
+// in column mode, the ghost slots [ghost, ghost + 2 * plane) (inlet plane, then
+// outlet plane).  Population p of global slot s sits at f[p * ns + s].  Every
+// per-step kernel is one launch over all slots of all instances; a thread finds
+// its node (packed x | y << 10 | z << 20, or kNoNode) and its instance (the
+// per-slot instance array, absent for a single instance) and reads the
+// instance's lattice, parameters and offsets from a small table.  Per-node
+// fields that stencils read (rho^N, n, link words, n_s) stay dense per instance,
+// at the instance's node offset; gidx maps each stored lattice position
+// (plane z + 1 in [0, nz + 1]) to a global slot, or -1 for a solid node.
+//
+// Storage type T: float (FP32) or __half (FP16 deviations from fixed reference
+// equilibria: f^r_i - w_i, f^p_i, g_j - w_j, i.e. reactant liquid at rest with
+// C = 1; all arithmetic in FP32).
 #pragma once
 #include <cuda_fp16.h>
 
 #include "kernels.cuh"
 
-// launch shapes (the defaults are the measured best on B300)
-#ifndef CGLBM_MAIN_BLOCK
-#define CGLBM_MAIN_BLOCK 128
-#endif
-#ifndef CGLBM_MAIN_MINB
-#define CGLBM_MAIN_MINB 8
-#endif
-#ifndef CGLBM_DENS_MINB
-#define CGLBM_DENS_MINB 1
-#endif
-
 namespace cglbm {
 
-struct Compact {
-  int nf;   // fluid slots
-  int ns;   // slot stride of one population (>= nf + ghost slots, multiple of 64)
+constexpr uint32_t kNoNode = 0xFFFFFFFFu;
+
+struct Inst {
+  Lattice L;
+  StepParams P;
+  int nf;        // fluid slots
+  int slot_off;  // first global fluid slot
+  int ghost;     // first global ghost slot (column mode)
+  int node_off;  // offset of the instance in the dense per-node fields
+  int gidx_off;  // offset of the instance in gidx
+  int pad;
 };
+
+struct Slots {
+  const Inst *__restrict__ inst;     // instance table
+  const uint16_t *__restrict__ kid;  // instance of each slot, or null (single instance)
+  const uint32_t *__restrict__ node; // packed coordinates of each slot, kNoNode for ghost / padding
+  int nslots;                        // slots covered by the launch grid
+  int ns;                            // population stride
+};
+
+__device__ __forceinline__ int slot_instance(const Slots &S, unsigned t) { return S.kid ? (int)S.kid[t] : 0; }
+
+__device__ __forceinline__ void unpack(uint32_t pk, int &x, int &y, int &z) {
+  x = (int)(pk & 1023u);
+  y = (int)((pk >> 10) & 1023u);
+  z = (int)((pk >> 20) & 2047u);
+}
 
 // reference value subtracted before FP16 storage of population p
 __device__ __forceinline__ float pop_ref(int p) { return p < Q ? W[p] : (p < 2 * Q ? 0.f : W7[p - 2 * Q]); }
@@ -57,19 +78,78 @@ struct Store<__half> {
   }
 };
 
-__device__ __forceinline__ void unpack(uint32_t pk, int &x, int &y, int &z) {
-  x = (int)(pk & 1023u);
-  y = (int)((pk >> 10) & 1023u);
-  z = (int)((pk >> 20) & 2047u);
+// Sum NV doubles of every thread of the block into acc[k * stride + j], k the
+// thread's instance: one atomic per value and block when the block holds one
+// instance (the usual case: slots are contiguous per instance), else per thread.
+template <int NV>
+__device__ __forceinline__ void block_accumulate_inst(double (&v)[NV], int k, double *acc, int stride) {
+  __shared__ double red[32][NV];
+  __shared__ int k0s;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) k0s = k;
+  __syncthreads();
+  const int k0 = k0s;
+  if (__syncthreads_and(k == k0)) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) red[warp][j] = v[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        double s = lane < nw ? red[lane][j] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0 && s != 0.0) atomicAdd(acc + (long long)k0 * stride + j, s);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (v[j] != 0.0) atomicAdd(acc + (long long)k * stride + j, v[j]);
+  }
+}
+
+// block sum of the reaction amounts into acc[4k] (cumulative) and acc[4k + 2 + slot]
+// (this step) of the threads' instance k (per thread when the block spans instances)
+__device__ __forceinline__ void block_delta_inst(double d, int k, double *acc, int slot) {
+  __shared__ double red[32];
+  __shared__ int k0s;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) k0s = k;
+  __syncthreads();
+  const int k0 = k0s;
+  if (__syncthreads_and(k == k0)) {
+    d = warp_sum(d);
+    if (lane == 0) red[warp] = d;
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+      double s = lane < nw ? red[lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0 && s != 0.0) {
+        atomicAdd(acc + 4 * k0, s);
+        atomicAdd(acc + 4 * k0 + 2 + slot, s);
+      }
+    }
+  } else if (d != 0.0) {
+    atomicAdd(acc + 4 * k, d);
+    atomicAdd(acc + 4 * k + 2 + slot, d);
+  }
 }
 
 // pull of the 45 (38) populations of fluid slot t at (x, y, z), halfway bounce-back
 // where the source is solid (gidx < 0)
 template <typename T>
-__device__ __forceinline__ void pull_compact(const Compact &C, const StepParams &P, const T *__restrict__ fin,
+__device__ __forceinline__ void pull_compact(int ns_, const StepParams &P, const T *__restrict__ fin,
                                              const int *__restrict__ gidx, const PullOffsets &O, unsigned t,
                                              float (&fr)[Q], float (&fp)[Q], float (&g)[Q7]) {
-  const unsigned ns = (unsigned)C.ns;
+  const unsigned ns = (unsigned)ns_;
   int src[Q];
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) src[i] = __ldg(gidx + O.src(CX[i], CY[i], CZ[i]));
@@ -96,61 +176,122 @@ __device__ __forceinline__ void pull_compact(const Compact &C, const StepParams 
 }
 
 // a1 + a2 over the fluid slots: colour function rho^N (dense field)
-template <typename T>
-__global__ void __launch_bounds__(256, CGLBM_DENS_MINB) k_density_c(Lattice L, Compact C, const T *__restrict__ f,
-                                                                    const int *__restrict__ gidx,
-                                                                    const uint32_t *__restrict__ cnode,
-                                                                    float *__restrict__ rhoN) {
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_density_c(Slots S, const T *__restrict__ f, const int *__restrict__ gidx,
+                                                   float *__restrict__ rhoN) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)C.nf) return;
+  if (t >= (unsigned)S.nslots) return;
+  const uint32_t pk = S.node[t];
+  if (pk == kNoNode) return;
+  const Inst &I = S.inst[slot_instance(S, t)];
   int x, y, z;
-  unpack(cnode[t], x, y, z);
+  unpack(pk, x, y, z);
   PullOffsets O;
-  O.init(L, x, y, z);
-  const unsigned ns = (unsigned)C.ns;
+  O.init(I.L, x, y, z);
+  const int *gi = gidx + I.gidx_off;
+  const unsigned ns = (unsigned)S.ns;
   float rr = 0.f, rp = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const int si = i == Q - 1 ? (int)t : __ldg(gidx + O.src(CX[i], CY[i], CZ[i]));
+    const int si = i == Q - 1 ? (int)t : __ldg(gi + O.src(CX[i], CY[i], CZ[i]));
     const bool bb = si < 0;
     const unsigned s = bb ? t : (unsigned)si;
     const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
     rr += Store<T>::ld(f, pr * ns + s, i);
     rp += Store<T>::ld(f, (pr + Q) * ns + s, Q + i);
   }
-  rhoN[nidx(L, x, y, z)] = (rr - rp) / (rr + rp);
+  rhoN[I.node_off + nidx(I.L, x, y, z)] = (rr - rp) / (rr + rp);
 }
 
-// a4 + a5 over the fluid slots (same arithmetic as k_normal)
-__global__ void __launch_bounds__(256) k_normal_c(Lattice L, StepParams P, Compact C,
-                                                  const uint32_t *__restrict__ cnode, const float *__restrict__ rhoN,
+// a4 + a5 over the fluid slots
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const float *__restrict__ rhoN,
                                                   const uint32_t *__restrict__ link, const float4 *__restrict__ ns,
                                                   float4 *__restrict__ nrm) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)C.nf) return;
+  if (t >= (unsigned)S.nslots) return;
+  const uint32_t pk = S.node[t];
+  if (pk == kNoNode) return;
+  const Inst &I = S.inst[slot_instance(S, t)];
   int x, y, z;
-  unpack(cnode[t], x, y, z);
-  StencilOffsets S;
-  S.init(L, x, y, z);
-  const unsigned node = S.own;
-  const uint32_t lk = link[node];
+  unpack(pk, x, y, z);
+  StencilOffsets St;
+  St.init(I.L, x, y, z);
+  const float *rn = rhoN + I.node_off;
+  const unsigned node = St.own;
   float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) {
-    const float v = 3.0f * W[i] * rhoN[S.nb(CX[i], CY[i], CZ[i])];
+    const float v = 3.0f * W[i] * rn[St.nb(CX[i], CY[i], CZ[i])];
     gx += CX[i] * v;
     gy += CY[i] * v;
     gz += CZ[i] * v;
   }
-  nrm[node] = wetted_normal(P, lk, ns, node, gx, gy, gz);
+  nrm[I.node_off + node] = wetted_normal(I.P, link[I.node_off + node], ns + I.node_off, node, gx, gy, gz);
+}
+
+// a3 / solid normals over the list of solid nodes next to the fluid (packed
+// coordinates, instance array kid or null); a solid node's link word marks in
+// bit i whether x + c_i is fluid
+__global__ void k_color_solid_c(const Inst *__restrict__ inst, const uint32_t *__restrict__ list,
+                                const uint16_t *__restrict__ kid, int count, const uint32_t *__restrict__ link,
+                                float *__restrict__ rhoN) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const Inst &I = inst[kid ? (int)kid[t] : 0];
+  int x, y, z;
+  unpack(list[t], x, y, z);
+  StencilOffsets St;
+  St.init(I.L, x, y, z);
+  float *rn = rhoN + I.node_off;
+  const uint32_t lk = link[I.node_off + St.own];
+  float num = 0.f, den = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    if ((lk >> i) & 1u) {
+      num += W[i] * rn[St.nb(CX[i], CY[i], CZ[i])];
+      den += W[i];
+    }
+  }
+  rn[St.own] = den > 0.f ? num / den : 0.f;
+}
+
+__global__ void k_normal_solid_c(const Inst *__restrict__ inst, const uint32_t *__restrict__ list,
+                                 const uint16_t *__restrict__ kid, int count, const uint32_t *__restrict__ link,
+                                 float4 *__restrict__ nrm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const Inst &I = inst[kid ? (int)kid[t] : 0];
+  int x, y, z;
+  unpack(list[t], x, y, z);
+  StencilOffsets St;
+  St.init(I.L, x, y, z);
+  float4 *nn = nrm + I.node_off;
+  const uint32_t lk = link[I.node_off + St.own];
+  float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    if ((lk >> i) & 1u) {
+      const float4 v = nn[St.nb(CX[i], CY[i], CZ[i])];
+      ax += W[i] * v.x;
+      ay += W[i] * v.y;
+      az += W[i] * v.z;
+    }
+  }
+  const float m = sqrtf(ax * ax + ay * ay + az * az);
+  if (m >= GRAD_EPS) {
+    const float inv = 1.0f / m;
+    nn[St.own] = make_float4(ax * inv, ay * inv, az * inv, 0.f);
+  } else {
+    nn[St.own] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 }
 
 // outlet ghost (column mode) of slot gs from the post-collision populations of a
 // fluid node of plane nz - 1 (same arithmetic as write_outlet_ghost)
 template <typename T>
-__device__ __forceinline__ void write_outlet_ghost_c(const Compact &C, T *__restrict__ f, unsigned gs,
-                                                     const float (&fr)[Q], const float (&fp)[Q], float g5,
-                                                     float rho_out) {
+__device__ __forceinline__ void write_outlet_ghost_c(int ns_, T *__restrict__ f, unsigned gs, const float (&fr)[Q],
+                                                     const float (&fp)[Q], float g5, float rho_out) {
   float rho = 0.f, rr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -165,7 +306,7 @@ __device__ __forceinline__ void write_outlet_ghost_c(const Compact &C, T *__rest
   const float vx = jx * inv, vy = jy * inv, vz = jz * inv;
   const float vv = vx * vx + vy * vy + vz * vz;
   const float psi = rr * inv;
-  const unsigned ns = (unsigned)C.ns;
+  const unsigned ns = (unsigned)ns_;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (CZ[i] != -1) continue;
@@ -176,72 +317,81 @@ __device__ __forceinline__ void write_outlet_ghost_c(const Compact &C, T *__rest
   Store<T>::st(f, (unsigned)(2 * Q + 5) * ns + gs, 2 * Q + 5, g5);
 }
 
-// a1, a2, a6 - a10 over the fluid slots; stores are coalesced and whole-sector
-template <typename T>
-__global__ void __launch_bounds__(CGLBM_MAIN_BLOCK, CGLBM_MAIN_MINB) k_main_c(
-    Lattice L, Compact C, StepParams P, const T *__restrict__ fin, T *__restrict__ fout,
-    const int *__restrict__ gidx, const uint32_t *__restrict__ cnode, const uint32_t *__restrict__ link,
-    const float4 *__restrict__ nrm, double *__restrict__ acc, int slot, float *__restrict__ dbg_H,
-    float *__restrict__ dbg_delta) {
+// a1, a2, a6 - a10 over the fluid slots; stores are coalesced and whole-sector.
+// acc holds 4 doubles per instance: cumulative delta, unused, per-step slots 0/1.
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, int n_inst, const T *__restrict__ fin,
+                                                               T *__restrict__ fout, const int *__restrict__ gidx,
+                                                               const uint32_t *__restrict__ link,
+                                                               const float4 *__restrict__ nrm, double *__restrict__ acc,
+                                                               int slot, float *__restrict__ dbg_H,
+                                                               float *__restrict__ dbg_delta) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  double dsum = 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) acc[2 + (slot ^ 1)] = 0.0;
-  if (t < (unsigned)C.nf) {
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) acc[4 * k + 2 + (slot ^ 1)] = 0.0;
+  double dsum[1] = {0.0};
+  const int k = slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1);
+  const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
+  if (pk != kNoNode) {
+    const Inst &I = S.inst[k];
     int x, y, z;
-    unpack(cnode[t], x, y, z);
-    StencilOffsets S;
-    S.init(L, x, y, z);
-    const unsigned node = S.own;
-    const uint32_t lk = link[node];
-    const float4 nme = nrm[node];
+    unpack(pk, x, y, z);
+    StencilOffsets St;
+    St.init(I.L, x, y, z);
+    const unsigned node = St.own;
+    const float4 *nn = nrm + I.node_off;
+    const uint32_t lk = link[I.node_off + node];
+    const float4 nme = nn[node];
     const float H =
-        nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nrm[S.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
+        nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nn[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
     PullOffsets O;
-    O.init(L, x, y, z);
+    O.init(I.L, x, y, z);
     float fr[Q], fp[Q], g[Q7];
-    pull_compact<T>(C, P, fin, gidx, O, t, fr, fp, g);
-    const float delta = collide_node(P, lk, fr, fp, g, nme, H);
-    const unsigned ns = (unsigned)C.ns;
+    pull_compact<T>(S.ns, I.P, fin, gidx + I.gidx_off, O, t, fr, fp, g);
+    const float delta = collide_node(I.P, lk, fr, fp, g, nme, H);
+    const unsigned ns = (unsigned)S.ns;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       Store<T>::st(fout, (unsigned)i * ns + t, i, fr[i]);
       Store<T>::st(fout, (unsigned)(Q + i) * ns + t, Q + i, fp[i]);
     }
     float g5;
-    if (P.reaction_mode == 0) {
+    if (I.P.reaction_mode == 0) {
 #pragma unroll
       for (int j = 0; j < Q7; ++j) Store<T>::st(fout, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j, g[j]);
       g5 = g[5];
     } else {
       g5 = Store<T>::ld(fin, (unsigned)(2 * Q + 5) * ns + t, 2 * Q + 5);
     }
-    if (L.bc_z == 1 && z == L.nz - 1) {
-      const unsigned gs = (unsigned)(C.nf + L.plane) + (unsigned)(y * L.nx + x);
-      write_outlet_ghost_c<T>(C, fout, gs, fr, fp, g5, P.rho_out);
+    if (I.L.bc_z == 1 && z == I.L.nz - 1) {
+      const unsigned gs = (unsigned)(I.ghost + I.L.plane) + (unsigned)(y * I.L.nx + x);
+      write_outlet_ghost_c<T>(S.ns, fout, gs, fr, fp, g5, I.P.rho_out);
     }
-    if (dbg_H) dbg_H[node] = H;
-    if (dbg_delta) dbg_delta[node] = delta;
-    dsum = (double)delta;
+    if (dbg_H) dbg_H[I.node_off + node] = H;
+    if (dbg_delta) dbg_delta[I.node_off + node] = delta;
+    dsum[0] = (double)delta;
   }
-  block_delta_sum(dsum, acc, slot);
+  // per instance: cumulative total acc[4k] and this step's slot acc[4k + 2 + slot]
+  block_delta_inst(dsum[0], k, acc, slot);
 }
 
-// equilibrium start of the fluid slots from dense fields (null: uniform values)
+// equilibrium start of instance I's fluid slots from dense fields (null: uniform values)
 template <typename T>
-__global__ void k_init_c(Lattice L, Compact C, const uint32_t *__restrict__ cnode, const float *__restrict__ rho_r,
+__global__ void k_init_c(Inst I, int ns_, const uint32_t *__restrict__ node, const float *__restrict__ rho_r,
                          const float *__restrict__ rho_p, const float *__restrict__ conc, const float *__restrict__ u,
                          float rr0, float rp0, float c0, T *__restrict__ fa, T *__restrict__ fb) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)C.nf) return;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= I.nf) return;
+  const unsigned t = (unsigned)(I.slot_off + l);
   int x, y, z;
-  unpack(cnode[t], x, y, z);
-  const long long node = nidx(L, x, y, z);
-  const float rr = rho_r ? rho_r[node] : rr0;
-  const float rp = rho_p ? rho_p[node] : rp0;
-  const float cc = conc ? conc[node] : c0;
-  const float ux = u ? u[node] : 0.f, uy = u ? u[L.n + node] : 0.f, uz = u ? u[2 * L.n + node] : 0.f;
+  unpack(node[t], x, y, z);
+  const long long nd = nidx(I.L, x, y, z);
+  const float rr = rho_r ? rho_r[nd] : rr0;
+  const float rp = rho_p ? rho_p[nd] : rp0;
+  const float cc = conc ? conc[nd] : c0;
+  const float ux = u ? u[nd] : 0.f, uy = u ? u[I.L.n + nd] : 0.f, uz = u ? u[2 * I.L.n + nd] : 0.f;
   const float uu = ux * ux + uy * uy + uz * uz;
-  const unsigned ns = (unsigned)C.ns;
+  const unsigned ns = (unsigned)ns_;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const float a = feq19(i, rr, ux, uy, uz, uu), b = feq19(i, rp, ux, uy, uz, uu);
@@ -259,16 +409,17 @@ __global__ void k_init_c(Lattice L, Compact C, const uint32_t *__restrict__ cnod
   }
 }
 
-// Column ghost slots of both buffers: constant inlet, outlet from plane nz - 1 of
-// fa (resting reactant equilibrium above solid nodes).
+// Column ghost slots of instance I in both buffers: constant inlet, outlet from
+// plane nz - 1 of fa (resting reactant equilibrium above solid nodes).
 template <typename T>
-__global__ void k_ghost_init_c(Lattice L, Compact C, const int *__restrict__ gidx, float u_in, float c_in,
-                               float rho_out, T *__restrict__ fa, T *__restrict__ fb) {
+__global__ void k_ghost_init_c(Inst I, int ns_, const int *__restrict__ gidx, float u_in, float c_in, float rho_out,
+                               T *__restrict__ fa, T *__restrict__ fb) {
+  const Lattice &L = I.L;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.nx || y >= L.ny) return;
-  const unsigned ns = (unsigned)C.ns;
-  const unsigned gin = (unsigned)C.nf + (unsigned)(y * L.nx + x);
+  const unsigned ns = (unsigned)ns_;
+  const unsigned gin = (unsigned)I.ghost + (unsigned)(y * L.nx + x);
   const unsigned gout = gin + (unsigned)L.plane;
   const float uu = u_in * u_in;
 #pragma unroll
@@ -288,7 +439,7 @@ __global__ void k_ghost_init_c(Lattice L, Compact C, const int *__restrict__ gid
   const float g4 = W7[4] * c_in * (1.0f + 4.0f * u_in);
   Store<T>::st(fa, (unsigned)(2 * Q + 4) * ns + gin, 2 * Q + 4, g4);
   Store<T>::st(fb, (unsigned)(2 * Q + 4) * ns + gin, 2 * Q + 4, g4);
-  const int s = gidx[(long long)L.nz * L.plane + (long long)y * L.nx + x];   // stored plane nz = z nz-1
+  const int s = gidx[I.gidx_off + (long long)L.nz * L.plane + (long long)y * L.nx + x];   // z = nz - 1
   if (s < 0) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -304,21 +455,24 @@ __global__ void k_ghost_init_c(Lattice L, Compact C, const int *__restrict__ gid
       fp[i] = Store<T>::ld(fa, (unsigned)(Q + i) * ns + (unsigned)s, Q + i);
     }
     const float g5 = Store<T>::ld(fa, (unsigned)(2 * Q + 5) * ns + (unsigned)s, 2 * Q + 5);
-    write_outlet_ghost_c<T>(C, fa, gout, fr, fp, g5, rho_out);
+    write_outlet_ghost_c<T>(ns_, fa, gout, fr, fp, g5, rho_out);
   }
 }
 
-// a11 over the fluid slots (FP32 per node, FP64 block accumulation); acc layout
-// as k_observables
+// a11 over the fluid slots (FP32 per node, FP64 block accumulation per instance).
+// obs holds 8 doubles per instance: mass_r, mass_p, mass_c, sum (1 - rho^N)/2,
+// flux_in, flux_out, n_bad.
 template <typename T>
-__global__ void k_observables_c(Lattice L, Compact C, const T *__restrict__ f, const uint32_t *__restrict__ cnode,
-                                double *__restrict__ acc) {
+__global__ void k_observables_c(Slots S, const T *__restrict__ f, double *__restrict__ obs) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  if (t < (unsigned)C.nf) {
+  const int k = slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1);
+  const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
+  if (pk != kNoNode) {
+    const Inst &I = S.inst[k];
     int x, y, z;
-    unpack(cnode[t], x, y, z);
-    const unsigned ns = (unsigned)C.ns;
+    unpack(pk, x, y, z);
+    const unsigned ns = (unsigned)S.ns;
     float rr = 0.f, rp = 0.f, cc = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -338,31 +492,33 @@ __global__ void k_observables_c(Lattice L, Compact C, const T *__restrict__ f, c
     if (!bad) {
       v[3] = 0.5f * (1.0f - (rr - rp) / rho);
       if (z == 0) v[4] = jz / rho * cc;
-      if (z == L.nz - 1) v[5] = jz / rho * cc;
+      if (z == I.L.nz - 1) v[5] = jz / rho * cc;
     }
     v[6] = bad ? 1.0 : 0.0;
   }
-  block_accumulate<7>(v, acc);
+  block_accumulate_inst<7>(v, k, obs, 8);
 }
 
-// state transfer helpers: stored populations of the fluid slots <-> FP32 values
-// in a [45][nf] buffer
+// state transfer helpers: stored populations of instance I's fluid slots <->
+// FP32 values in a [45][nf] buffer
 template <typename T>
-__global__ void k_slots_to_f32(Compact C, const T *__restrict__ src, float *__restrict__ dst) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)C.nf) return;
+__global__ void k_slots_to_f32(Inst I, int ns_, const T *__restrict__ src, float *__restrict__ dst) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= I.nf) return;
+  const unsigned t = (unsigned)(I.slot_off + l);
 #pragma unroll
-  for (int p = 0; p < NPOP; ++p) dst[(size_t)p * C.nf + t] = Store<T>::ld(src, (unsigned)p * C.ns + t, p);
+  for (int p = 0; p < NPOP; ++p) dst[(size_t)p * I.nf + l] = Store<T>::ld(src, (unsigned)p * (unsigned)ns_ + t, p);
 }
 template <typename T>
-__global__ void k_f32_to_slots(Compact C, const float *__restrict__ src, T *__restrict__ a, T *__restrict__ b) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)C.nf) return;
+__global__ void k_f32_to_slots(Inst I, int ns_, const float *__restrict__ src, T *__restrict__ a, T *__restrict__ b) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= I.nf) return;
+  const unsigned t = (unsigned)(I.slot_off + l);
 #pragma unroll
   for (int p = 0; p < NPOP; ++p) {
-    const float v = src[(size_t)p * C.nf + t];
-    Store<T>::st(a, (unsigned)p * C.ns + t, p, v);
-    Store<T>::st(b, (unsigned)p * C.ns + t, p, v);
+    const float v = src[(size_t)p * I.nf + l];
+    Store<T>::st(a, (unsigned)p * (unsigned)ns_ + t, p, v);
+    Store<T>::st(b, (unsigned)p * (unsigned)ns_ + t, p, v);
   }
 }
 

@@ -30,7 +30,10 @@ KERNEL_NAMES = ("density", "color_solid", "normal", "normal_solid", "main", "obs
 SYMBOLS = (
     "lbm_create", "lbm_step", "lbm_observables", "lbm_reaction", "lbm_init_fields", "lbm_get_state",
     "lbm_set_state", "lbm_get_field", "lbm_set_debug", "lbm_profile", "lbm_profile_read",
-    "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static",
+    "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static", "lbm_tune",
+    "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables", "lbm_batch_get_state",
+    "lbm_batch_set_state", "lbm_batch_tune", "lbm_batch_profile", "lbm_batch_profile_read",
+    "lbm_batch_destroy",
 )
 STATIC_MAX_NODES = 131072   # LBM_STATIC_MAX_NODES
 
@@ -120,6 +123,17 @@ def load_library(path=LIB_PATH):
         "lbm_destroy": (None, [P]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_step_static": (ctypes.c_int, [I32, I32, I32, P, P, P, P, P, ctypes.POINTER(_Params)]),
+        "lbm_tune": (ctypes.c_int, [P, P]),
+        "lbm_batch_create": (ctypes.c_int, [I32, ctypes.POINTER(_Geometry), ctypes.POINTER(_Params), P,
+                                            ctypes.POINTER(P)]),
+        "lbm_batch_step": (ctypes.c_int, [P, I64]),
+        "lbm_batch_observables": (ctypes.c_int, [P, ctypes.POINTER(_Obs), I32]),
+        "lbm_batch_get_state": (ctypes.c_int, [P, I32, P, SZ]),
+        "lbm_batch_set_state": (ctypes.c_int, [P, I32, P, SZ]),
+        "lbm_batch_tune": (ctypes.c_int, [P, P]),
+        "lbm_batch_profile": (ctypes.c_int, [P, I32]),
+        "lbm_batch_profile_read": (ctypes.c_int, [P, P, P, I32]),
+        "lbm_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +240,13 @@ def lbm_info(ctx):
     return dict(n_fluid=v[0].value, n_wall=v[1].value, n_solid_bnd=v[2].value, device_bytes=v[3].value)
 
 
+def lbm_tune(ctx):
+    """Time the candidate launch shapes on the current state and keep the fastest; returns them."""
+    blocks = np.zeros(3, dtype=np.int32)
+    _check(load_library().lbm_tune(ctx, _ptr(blocks)), "lbm_tune")
+    return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]))
+
+
 def lbm_destroy(ctx):
     if ctx is not None and ctx.value:
         load_library().lbm_destroy(ctx)
@@ -246,6 +267,36 @@ def lbm_step_static(shape, solid_dev, f_in_dev, f_out_dev, params, reactive_dev=
     p = params.to_c(stream)
     _check(load_library().lbm_step_static(int(nx), int(ny), int(nz), solid_dev, reactive_dev, f_in_dev, f_out_dev,
                                            delta_sum_dev, ctypes.byref(p)), "lbm_step_static")
+
+
+def _geometry(solid, reactive, bc_z):
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    if solid.ndim != 3:
+        raise LbmError(LBM_EINVAL, "solid must be a (nz, ny, nx) array")
+    react = None if reactive is None else np.ascontiguousarray(reactive, dtype=np.uint8)
+    if react is not None and react.shape != solid.shape:
+        raise LbmError(LBM_EINVAL, "reactive mask shape")
+    nz, ny, nx = solid.shape
+    g = _Geometry(nx, ny, nz, solid.ctypes.data, react.ctypes.data if react is not None else None, int(bc_z))
+    return g, (solid, react)
+
+
+def lbm_batch_create(solids, params, reactives=None, bc_z=None, stream=None):
+    """Create a batch of independent lattices (lists of masks, Params, optional r masks, bc_z)."""
+    lib = load_library()
+    n = len(solids)
+    reactives = reactives or [None] * n
+    bc_z = bc_z if bc_z is not None else [0] * n
+    geoms = (_Geometry * n)()
+    keep = []
+    for k in range(n):
+        g, arrays = _geometry(solids[k], reactives[k], bc_z[k])
+        geoms[k] = g
+        keep.append(arrays)
+    prms = (_Params * n)(*[p.to_c(stream) for p in params])
+    h = ctypes.c_void_p()
+    _check(lib.lbm_batch_create(n, geoms, prms, stream, ctypes.byref(h)), "lbm_batch_create")
+    return h
 
 
 # --------------------------------------------------------------------------- convenience
@@ -291,10 +342,74 @@ class Lattice:
     def info(self):
         return lbm_info(self.ctx)
 
+    def tune(self):
+        return lbm_tune(self.ctx)
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             lbm_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent lattices advanced together (one launch per kernel for all of them)."""
+
+    def __init__(self, solids, params, reactives=None, bc_z=None, stream=None):
+        self.shapes = [tuple(np.shape(s)) for s in solids]
+        self.n = len(solids)
+        self.handle = lbm_batch_create(solids, params, reactives, bc_z, stream)
+
+    def step(self, n=1):
+        _check(load_library().lbm_batch_step(self.handle, int(n)), "lbm_batch_step")
+
+    def observables(self, allow_nan=False):
+        obs = (_Obs * self.n)()
+        rc = load_library().lbm_batch_observables(self.handle, obs, self.n)
+        if rc != LBM_OK and not (allow_nan and rc == LBM_ENAN):
+            _check(rc, "lbm_batch_observables")
+        return [{nm: getattr(o, nm) for nm, _ in _Obs._fields_} for o in obs]
+
+    def get_state(self, k):
+        nz, ny, nx = self.shapes[k]
+        out = np.empty((NPOP, nz, ny, nx), dtype=np.float32)
+        _check(load_library().lbm_batch_get_state(self.handle, int(k), _ptr(out), out.nbytes), "lbm_batch_get_state")
+        return out
+
+    def set_state(self, k, f):
+        f = np.ascontiguousarray(f, dtype=np.float32)
+        _check(load_library().lbm_batch_set_state(self.handle, int(k), _ptr(f), f.nbytes), "lbm_batch_set_state")
+
+    def tune(self):
+        blocks = np.zeros(3, dtype=np.int32)
+        _check(load_library().lbm_batch_tune(self.handle, _ptr(blocks)), "lbm_batch_tune")
+        return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]))
+
+    def profile(self, max_launches):
+        _check(load_library().lbm_batch_profile(self.handle, int(max_launches)), "lbm_batch_profile")
+
+    def profile_read(self):
+        ms = np.zeros(len(KERNEL_NAMES), dtype=np.float64)
+        n = np.zeros(len(KERNEL_NAMES), dtype=np.int64)
+        _check(load_library().lbm_batch_profile_read(self.handle, _ptr(ms), _ptr(n), len(KERNEL_NAMES)),
+               "lbm_batch_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().lbm_batch_destroy(self.handle)
+        self.handle = None
 
     def __enter__(self):
         return self

@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % HBM roofline at 1 B300 (plain vs FP16-storage/batched/adjoint)"
 UNIT = "MLUPS"
-KERNELS_SRC = os.path.join(ROOT, "paper_2608_15781_b300", "csrc", "kernels.cuh")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2608_15781_b300", "csrc", f)
+                  for f in ("lattice.cuh", "kernels.cuh", "compact.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_main_dram_traffic.txt")
 
 
@@ -67,8 +68,12 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    with open(KERNELS_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the device sources of the step kernels."""
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic_per_fluid_node():
@@ -81,7 +86,7 @@ def ncu_traffic_per_fluid_node():
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 kv[k.strip()] = v.strip()
-    if kv.get("kernels_cuh_sha256_16") != kernel_source_hash():
+    if kv.get("kernel_sources_sha256_16") != kernel_source_hash():
         return None
     try:
         return float(kv["dram_bytes_per_fluid_node"])
@@ -315,6 +320,9 @@ def run_native(args):
                          "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
             "conversion": obv["conversion"], "gas_saturation": obv["gas_saturation"]}
 
+    if not args.no_variants:
+        variants["batched"] = measure_batched(lbm, torch, stream, world, max(args.steps // 10, 20), args.warmup)
+
     # end to end through the C ABI with host buffers: create from the host mask,
     # K x (step + read of the step's reaction sums), observables, destroy
     e2e = None
@@ -376,6 +384,55 @@ def run_native(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def measure_batched(lbm, torch, stream, world, steps, warmup, seq_steps=20):
+    """64 uneven columns (48^3 - 96^3) in one batch against the same 64 lattices run one after another."""
+    from paper_2608_15781_b300.configs import batched_workload
+
+    masks, params, bcs, edges = batched_workload()
+    nodes = sum(int(np.prod(m.shape)) for m in masks)
+    B = lbm.Batch(masks, params, bc_z=bcs, stream=stream.cuda_stream)
+    B.step(warmup)
+    blocks = B.tune()
+    B.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1)
+    B.profile(steps * 6 + 16)
+    B.step(steps)
+    prof = B.profile_read()
+    B.profile(0)
+    obs = B.observables()
+    nf = sum(o["n_fluid"] for o in obs)
+    B.close()
+    # the same lattices one after another, each through its own context (graph replay too)
+    t_s = 0.0
+    for m, p, bc in zip(masks, params, bcs):
+        L = lbm.Lattice(m, p, bc_z=bc, stream=stream.cuda_stream)
+        L.step(warmup)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(seq_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_s += e0.elapsed_time(e1)
+        L.close()
+    k_ms, k_n = prof["main"]
+    peak, _ = measured_peaks()
+    alg = nf * bytes_per_fluid_node(params[0])
+    achieved = alg / (k_ms / k_n * 1e-3) / 1e9
+    v_b = world * nodes * steps / (t_b * 1e-3) / 1e6
+    v_s = nodes * seq_steps / (t_s * 1e-3) / 1e6
+    return {"value": round(v_b, 2), "unit": UNIT, "steps": steps, "ms_per_step": round(t_b / steps, 5),
+            "workload": f"64 columns, edges {min(edges)}-{max(edges)}, {nodes} nodes, {nf} fluid",
+            "blocks": blocks, "sequential_value": round(v_s, 2), "speedup_vs_sequential": round(v_b / v_s, 3),
+            "roofline": {"kernel": "k_main", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4)}}
 
 
 def main():

@@ -40,6 +40,10 @@ WORKLOADS = {
     "column128x128x256": Workload("column128x128x256", (256, 128, 128), 8, 0.5, 2, 1,
                                   Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=5e-3,
                                          diffusivity=0.05, u_in=0.005, c_in=1.0, c_init=1.0, rho_out=1.0)),
+    # the same column recipe at a quarter of the length: small case of the kernel profiles
+    "column128x128x64": Workload("column128x128x64", (64, 128, 128), 8, 0.5, 2, 1,
+                                 Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=5e-3,
+                                        diffusivity=0.05, u_in=0.005, c_in=1.0, c_init=1.0, rho_out=1.0)),
     # 256^3 periodic precision workload
     "periodic256": Workload("periodic256", (256, 256, 256), 12, 0.5, 3, 0,
                             Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=1e-3,
@@ -48,3 +52,24 @@ WORKLOADS = {
     "column96": Workload("column96", (96, 96, 96), 6, 0.5, 5, 1,
                          Params(theta_deg=60.0, k_rate=2e-3, u_in=0.004, c_in=1.0)),
 }
+
+
+def batched_workload(n=64, seed0=100, draw_seed=4242):
+    """64 independent columns of uneven size: cube edge uniform in 48..96, porosity
+    uniform in [0.4, 0.6], contact angle uniform in [20, 120] degrees, inlet velocity
+    uniform in [0.001, 0.01]; mask k uses GRF seed seed0 + k with shell |k| = edge/16.
+    Returns (masks, params, bc_z, edges)."""
+    u = synth.uniform01(draw_seed, 4 * n).reshape(n, 4)
+    masks, params, edges = [], [], []
+    for k in range(n):
+        edge = 48 + int(u[k, 0] * 49)            # 48 .. 96
+        edge = min(edge, 96)
+        phi = 0.4 + 0.2 * u[k, 1]
+        theta = 20.0 + 100.0 * u[k, 2]
+        u_in = 0.001 + 0.009 * u[k, 3]
+        masks.append(synth.grf_mask((edge, edge, edge), max(2, round(edge / 16)), phi, seed0 + k,
+                                    periodic_z=False))
+        params.append(Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=theta, k_rate=5e-3, diffusivity=0.05,
+                             u_in=u_in, c_in=1.0, c_init=1.0))
+        edges.append(edge)
+    return masks, params, [1] * n, edges

@@ -203,41 +203,86 @@ void with_storage(const Batch &b, F &&f) {
 
 Slots slots(const Batch &b) { return Slots{b.inst, b.kid, b.node, b.nslots, b.ns}; }
 
+template <typename T, bool BT>
+void launch_density_t(const Batch &b, cudaStream_t st, const void *fin) {
+  const Slots S = slots(b);
+  const Inst &I = b.h[0].d;
+  switch (b.dens_block) {
+    case 128:
+      k_density_c<T, 128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, (const T *)fin, b.gidx, b.rhoN);
+      break;
+    case 512:
+      k_density_c<T, 512, BT><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, I, (const T *)fin, b.gidx, b.rhoN);
+      break;
+    default:
+      k_density_c<T, 256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, (const T *)fin, b.gidx, b.rhoN);
+  }
+}
 template <typename T>
 void launch_density(const Batch &b, cudaStream_t st, const void *fin) {
-  const Slots S = slots(b);
-  switch (b.dens_block) {
-    case 128: k_density_c<T, 128><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, (const T *)fin, b.gidx, b.rhoN); break;
-    case 512: k_density_c<T, 512><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, (const T *)fin, b.gidx, b.rhoN); break;
-    default: k_density_c<T, 256><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, (const T *)fin, b.gidx, b.rhoN);
-  }
+  if (b.n > 1)
+    launch_density_t<T, true>(b, st, fin);
+  else
+    launch_density_t<T, false>(b, st, fin);
 }
 
-void launch_normal(const Batch &b, cudaStream_t st) {
+template <bool BT>
+void launch_normal_t(const Batch &b, cudaStream_t st) {
   const Slots S = slots(b);
+  const Inst &I = b.h[0].d;
   switch (b.norm_block) {
-    case 128: k_normal_c<128><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, b.rhoN, b.link, b.nsv, b.nrm); break;
-    case 512: k_normal_c<512><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, b.rhoN, b.link, b.nsv, b.nrm); break;
-    default: k_normal_c<256><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, b.rhoN, b.link, b.nsv, b.nrm);
+    case 128: k_normal_c<128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, b.nrm); break;
+    case 512: k_normal_c<512, BT><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, b.nrm); break;
+    default: k_normal_c<256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, b.nrm);
   }
 }
+void launch_normal(const Batch &b, cudaStream_t st) {
+  if (b.n > 1)
+    launch_normal_t<true>(b, st);
+  else
+    launch_normal_t<false>(b, st);
+}
 
-template <typename T>
-void launch_main(const Batch &b, cudaStream_t st, const void *fin, void *fout, double *acc, int slot) {
+template <typename T, bool BT>
+void launch_main_t(const Batch &b, cudaStream_t st, const void *fin, void *fout, double *acc, int slot) {
   const Slots S = slots(b);
+  const Inst &I = b.h[0].d;
   float *dh = b.debug ? b.dbg_H : nullptr, *dd = b.debug ? b.dbg_delta : nullptr;
   switch (b.main_block) {
     case 64:
-      k_main_c<T, 64><<<(S.nslots + 63) / 64, 64, 0, st>>>(S, b.n, (const T *)fin, (T *)fout, b.gidx, b.link, b.nrm,
-                                                          acc, slot, dh, dd);
+      k_main_c<T, 64, BT><<<(S.nslots + 63) / 64, 64, 0, st>>>(S, I, b.n, (const T *)fin, (T *)fout, b.gidx, b.link,
+                                                              b.nrm, acc, slot, dh, dd);
       break;
     case 256:
-      k_main_c<T, 256><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, b.n, (const T *)fin, (T *)fout, b.gidx, b.link,
-                                                              b.nrm, acc, slot, dh, dd);
+      k_main_c<T, 256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, b.n, (const T *)fin, (T *)fout, b.gidx,
+                                                                  b.link, b.nrm, acc, slot, dh, dd);
       break;
     default:
-      k_main_c<T, 128><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, b.n, (const T *)fin, (T *)fout, b.gidx, b.link,
-                                                              b.nrm, acc, slot, dh, dd);
+      k_main_c<T, 128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, b.n, (const T *)fin, (T *)fout, b.gidx,
+                                                                  b.link, b.nrm, acc, slot, dh, dd);
+  }
+}
+template <typename T>
+void launch_main(const Batch &b, cudaStream_t st, const void *fin, void *fout, double *acc, int slot) {
+  if (b.n > 1)
+    launch_main_t<T, true>(b, st, fin, fout, acc, slot);
+  else
+    launch_main_t<T, false>(b, st, fin, fout, acc, slot);
+}
+
+void launch_solids(const Batch &b, cudaStream_t st, bool colour) {
+  const Inst &I = b.h[0].d;
+  const unsigned g = (unsigned)((b.n_bnd + 255) / 256);
+  if (colour) {
+    if (b.n > 1)
+      k_color_solid_c<true><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+    else
+      k_color_solid_c<false><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+  } else {
+    if (b.n > 1)
+      k_normal_solid_c<true><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+    else
+      k_normal_solid_c<false><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
   }
 }
 
@@ -252,7 +297,7 @@ void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int sl
     pe();
     if (b.n_bnd > 0) {
       pb(1);
-      k_color_solid_c<<<(b.n_bnd + 255) / 256, 256, 0, st>>>(b.inst, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+      launch_solids(b, st, true);
       pe();
     }
     pb(2);
@@ -260,7 +305,7 @@ void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int sl
     pe();
     if (b.n_bnd > 0) {
       pb(3);
-      k_normal_solid_c<<<(b.n_bnd + 255) / 256, 256, 0, st>>>(b.inst, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+      launch_solids(b, st, false);
       pe();
     }
     pb(4);
@@ -304,7 +349,12 @@ int launch_observables(Batch &b) {
   prof_begin(b, 5, b.stream);
   with_storage(b, [&](auto *tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
-    k_observables_c<T><<<(b.nslots + 255) / 256, 256, 0, b.stream>>>(slots(b), (const T *)b.fa, b.obs);
+    if (b.n > 1)
+      k_observables_c<T, true><<<(b.nslots + 255) / 256, 256, 0, b.stream>>>(slots(b), b.h[0].d, (const T *)b.fa,
+                                                                             b.obs);
+    else
+      k_observables_c<T, false><<<(b.nslots + 255) / 256, 256, 0, b.stream>>>(slots(b), b.h[0].d, (const T *)b.fa,
+                                                                              b.obs);
   });
   prof_end(b, b.stream);
   CK(cudaGetLastError());

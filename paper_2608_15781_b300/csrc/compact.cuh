@@ -116,15 +116,19 @@ __device__ __forceinline__ void block_accumulate_inst(double (&v)[NV], int k, do
 
 // block sum of the reaction amounts into acc[4k] (cumulative) and acc[4k + 2 + slot]
 // (this step) of the threads' instance k (per thread when the block spans instances)
+template <bool BATCH>
 __device__ __forceinline__ void block_delta_inst(double d, int k, double *acc, int slot) {
   __shared__ double red[32];
   __shared__ int k0s;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) k0s = k;
-  __syncthreads();
-  const int k0 = k0s;
-  if (__syncthreads_and(k == k0)) {
+  int k0 = 0;
+  if (BATCH) {
+    if (tid == 0) k0s = k;
+    __syncthreads();
+    k0 = k0s;
+  }
+  if (!BATCH || __syncthreads_and(k == k0)) {
     d = warp_sum(d);
     if (lane == 0) red[warp] = d;
     __syncthreads();
@@ -176,19 +180,28 @@ __device__ __forceinline__ void pull_compact(int ns_, const StepParams &P, const
 }
 
 // a1 + a2 over the fluid slots: colour function rho^N (dense field)
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_density_c(Slots S, const T *__restrict__ f, const int *__restrict__ gidx,
-                                                   float *__restrict__ rhoN) {
+// With BATCH false the kernel serves one lattice whose table entry travels as a
+// kernel parameter (constant bank); with BATCH true each thread reads its
+// lattice's entry from the table.
+template <bool BATCH>
+__device__ __forceinline__ const Inst &inst_of(const Slots &S, const Inst &single, int k) {
+  return BATCH ? S.inst[k] : single;
+}
+
+template <typename T, int BLOCK, bool BATCH>
+__global__ void __launch_bounds__(BLOCK) k_density_c(Slots S, const __grid_constant__ Inst single,
+                                                     const T *__restrict__ f, const int *__restrict__ gidx,
+                                                     float *__restrict__ rhoN) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)S.nslots) return;
   const uint32_t pk = S.node[t];
   if (pk == kNoNode) return;
-  const Inst &I = S.inst[slot_instance(S, t)];
+  const Inst &I = inst_of<BATCH>(S, single, BATCH ? slot_instance(S, t) : 0);
   int x, y, z;
   unpack(pk, x, y, z);
   PullOffsets O;
   O.init(I.L, x, y, z);
-  const int *gi = gidx + I.gidx_off;
+  const int *gi = gidx + (BATCH ? I.gidx_off : 0);
   const unsigned ns = (unsigned)S.ns;
   float rr = 0.f, rp = 0.f;
 #pragma unroll
@@ -200,24 +213,24 @@ __global__ void __launch_bounds__(BLOCK) k_density_c(Slots S, const T *__restric
     rr += Store<T>::ld(f, pr * ns + s, i);
     rp += Store<T>::ld(f, (pr + Q) * ns + s, Q + i);
   }
-  rhoN[I.node_off + nidx(I.L, x, y, z)] = (rr - rp) / (rr + rp);
+  rhoN[(BATCH ? I.node_off : 0) + nidx(I.L, x, y, z)] = (rr - rp) / (rr + rp);
 }
 
 // a4 + a5 over the fluid slots
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const float *__restrict__ rhoN,
-                                                  const uint32_t *__restrict__ link, const float4 *__restrict__ ns,
-                                                  float4 *__restrict__ nrm) {
+template <int BLOCK, bool BATCH>
+__global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const __grid_constant__ Inst single,
+                                                    const float *__restrict__ rhoN, const uint32_t *__restrict__ link,
+                                                    const float4 *__restrict__ ns, float4 *__restrict__ nrm) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)S.nslots) return;
   const uint32_t pk = S.node[t];
   if (pk == kNoNode) return;
-  const Inst &I = S.inst[slot_instance(S, t)];
+  const Inst &I = inst_of<BATCH>(S, single, BATCH ? slot_instance(S, t) : 0);
   int x, y, z;
   unpack(pk, x, y, z);
   StencilOffsets St;
   St.init(I.L, x, y, z);
-  const float *rn = rhoN + I.node_off;
+  const float *rn = rhoN + (BATCH ? I.node_off : 0);
   const unsigned node = St.own;
   float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
@@ -227,18 +240,20 @@ __global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const float *__rest
     gy += CY[i] * v;
     gz += CZ[i] * v;
   }
-  nrm[I.node_off + node] = wetted_normal(I.P, link[I.node_off + node], ns + I.node_off, node, gx, gy, gz);
+  const int noff = BATCH ? I.node_off : 0;
+  nrm[noff + node] = wetted_normal(I.P, link[noff + node], ns + noff, node, gx, gy, gz);
 }
 
 // a3 / solid normals over the list of solid nodes next to the fluid (packed
 // coordinates, instance array kid or null); a solid node's link word marks in
 // bit i whether x + c_i is fluid
-__global__ void k_color_solid_c(const Inst *__restrict__ inst, const uint32_t *__restrict__ list,
-                                const uint16_t *__restrict__ kid, int count, const uint32_t *__restrict__ link,
-                                float *__restrict__ rhoN) {
+template <bool BATCH>
+__global__ void k_color_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
+                                const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
+                                const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const Inst &I = inst[kid ? (int)kid[t] : 0];
+  const Inst &I = BATCH ? inst[kid[t]] : single;
   int x, y, z;
   unpack(list[t], x, y, z);
   StencilOffsets St;
@@ -256,12 +271,13 @@ __global__ void k_color_solid_c(const Inst *__restrict__ inst, const uint32_t *_
   rn[St.own] = den > 0.f ? num / den : 0.f;
 }
 
-__global__ void k_normal_solid_c(const Inst *__restrict__ inst, const uint32_t *__restrict__ list,
-                                 const uint16_t *__restrict__ kid, int count, const uint32_t *__restrict__ link,
-                                 float4 *__restrict__ nrm) {
+template <bool BATCH>
+__global__ void k_normal_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
+                                 const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
+                                 const uint32_t *__restrict__ link, float4 *__restrict__ nrm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const Inst &I = inst[kid ? (int)kid[t] : 0];
+  const Inst &I = BATCH ? inst[kid[t]] : single;
   int x, y, z;
   unpack(list[t], x, y, z);
   StencilOffsets St;
@@ -319,35 +335,42 @@ __device__ __forceinline__ void write_outlet_ghost_c(int ns_, T *__restrict__ f,
 
 // a1, a2, a6 - a10 over the fluid slots; stores are coalesced and whole-sector.
 // acc holds 4 doubles per instance: cumulative delta, unused, per-step slots 0/1.
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, int n_inst, const T *__restrict__ fin,
+template <typename T, int BLOCK, bool BATCH>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const __grid_constant__ Inst single,
+                                                               int n_inst, const T *__restrict__ fin,
                                                                T *__restrict__ fout, const int *__restrict__ gidx,
                                                                const uint32_t *__restrict__ link,
                                                                const float4 *__restrict__ nrm, double *__restrict__ acc,
                                                                int slot, float *__restrict__ dbg_H,
                                                                float *__restrict__ dbg_delta) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0)
-    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) acc[4 * k + 2 + (slot ^ 1)] = 0.0;
+  if (blockIdx.x == 0) {
+    if (BATCH) {
+      for (int k = threadIdx.x; k < n_inst; k += blockDim.x) acc[4 * k + 2 + (slot ^ 1)] = 0.0;
+    } else if (threadIdx.x == 0) {
+      acc[2 + (slot ^ 1)] = 0.0;
+    }
+  }
   double dsum[1] = {0.0};
-  const int k = slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1);
+  const int k = BATCH ? slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1) : 0;
   const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
   if (pk != kNoNode) {
-    const Inst &I = S.inst[k];
+    const Inst &I = inst_of<BATCH>(S, single, k);
     int x, y, z;
     unpack(pk, x, y, z);
     StencilOffsets St;
     St.init(I.L, x, y, z);
     const unsigned node = St.own;
-    const float4 *nn = nrm + I.node_off;
-    const uint32_t lk = link[I.node_off + node];
+    const int noff = BATCH ? I.node_off : 0;
+    const float4 *nn = nrm + noff;
+    const uint32_t lk = link[noff + node];
     const float4 nme = nn[node];
     const float H =
         nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nn[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
     PullOffsets O;
     O.init(I.L, x, y, z);
     float fr[Q], fp[Q], g[Q7];
-    pull_compact<T>(S.ns, I.P, fin, gidx + I.gidx_off, O, t, fr, fp, g);
+    pull_compact<T>(S.ns, I.P, fin, gidx + (BATCH ? I.gidx_off : 0), O, t, fr, fp, g);
     const float delta = collide_node(I.P, lk, fr, fp, g, nme, H);
     const unsigned ns = (unsigned)S.ns;
 #pragma unroll
@@ -367,12 +390,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, int n_i
       const unsigned gs = (unsigned)(I.ghost + I.L.plane) + (unsigned)(y * I.L.nx + x);
       write_outlet_ghost_c<T>(S.ns, fout, gs, fr, fp, g5, I.P.rho_out);
     }
-    if (dbg_H) dbg_H[I.node_off + node] = H;
-    if (dbg_delta) dbg_delta[I.node_off + node] = delta;
+    if (dbg_H) dbg_H[noff + node] = H;
+    if (dbg_delta) dbg_delta[noff + node] = delta;
     dsum[0] = (double)delta;
   }
   // per instance: cumulative total acc[4k] and this step's slot acc[4k + 2 + slot]
-  block_delta_inst(dsum[0], k, acc, slot);
+  block_delta_inst<BATCH>(dsum[0], k, acc, slot);
 }
 
 // equilibrium start of instance I's fluid slots from dense fields (null: uniform values)
@@ -462,14 +485,15 @@ __global__ void k_ghost_init_c(Inst I, int ns_, const int *__restrict__ gidx, fl
 // a11 over the fluid slots (FP32 per node, FP64 block accumulation per instance).
 // obs holds 8 doubles per instance: mass_r, mass_p, mass_c, sum (1 - rho^N)/2,
 // flux_in, flux_out, n_bad.
-template <typename T>
-__global__ void k_observables_c(Slots S, const T *__restrict__ f, double *__restrict__ obs) {
+template <typename T, bool BATCH>
+__global__ void k_observables_c(Slots S, const __grid_constant__ Inst single, const T *__restrict__ f,
+                                double *__restrict__ obs) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  const int k = slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1);
+  const int k = BATCH ? slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1) : 0;
   const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
   if (pk != kNoNode) {
-    const Inst &I = S.inst[k];
+    const Inst &I = inst_of<BATCH>(S, single, k);
     int x, y, z;
     unpack(pk, x, y, z);
     const unsigned ns = (unsigned)S.ns;

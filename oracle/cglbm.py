@@ -141,6 +141,8 @@ class Geometry:
     ns: np.ndarray = field(init=False)          # solid normal at wall nodes, shape (3, ...)
     ns_ok: np.ndarray = field(init=False)       # n_s defined (non-zero stencil sum)
     reactive_mask: np.ndarray = None            # optional user r(x)
+    theta_deg: np.ndarray = None                # optional per-node contact angle, read at solid nodes
+    theta_wall: np.ndarray = field(init=False)  # contact angle seen by each wall node (degrees) or None
 
     def __post_init__(self):
         s = self.solid.astype(bool)
@@ -173,10 +175,28 @@ class Geometry:
         mag = np.sqrt((acc * acc).sum(axis=0))
         self.ns_ok = self.wall & (mag > 0.0)
         self.ns = np.where(self.ns_ok, acc / np.where(mag > 0.0, mag, 1.0), 0.0)
+        self.theta_wall = None if self.theta_deg is None else wall_contact_angle(self.theta_deg, s, self.bc_z)
 
     @property
     def shape(self):
         return self.solid.shape
+
+
+def wall_contact_angle(theta_deg, solid, bc_z):
+    """Contact angle at every fluid node from a per-solid-node field (our reading of a
+    spatially varying wettability, which the paper keeps uniform): the D3Q19-weighted
+    mean of theta over the solid neighbours x + c_i (geometry stencil), defined where
+    there is at least one; 0 elsewhere.  Uniform theta gives that value."""
+    s = np.asarray(solid, dtype=bool)
+    th = np.asarray(theta_deg, dtype=np.float64)
+    zm = _zmode(bc_z)
+    num = np.zeros(s.shape)
+    den = np.zeros(s.shape)
+    for i in range(Q19 - 1):
+        sn = neighbor(s, C19[i], zm).astype(np.float64)
+        num += W19L[i] * sn * neighbor(th, C19[i], zm)
+        den += W19L[i] * sn
+    return np.where(den > 0.0, num / np.where(den > 0.0, den, 1.0), 0.0)
 
 
 # ---------------------------------------------------------------------------
@@ -338,8 +358,17 @@ def gradient(phi, geom):
 
 
 def wetting(n, geom, params):
-    """a5, Eq. realigned_normal_vectors at wall nodes; keeps whichever of n_+/n_- is closer to n."""
-    th = math.radians(params.theta_deg)
+    """a5, Eq. realigned_normal_vectors at wall nodes; keeps whichever of n_+/n_- is closer to n.
+
+    theta is params.theta_deg, or per node geom.theta_wall when the geometry carries
+    a per-solid-node contact angle.
+    """
+    if geom.theta_wall is None:
+        th = math.radians(params.theta_deg)
+        cos_th, sin_th = math.cos(th), math.sin(th)
+    else:
+        th = np.radians(geom.theta_wall)
+        cos_th, sin_th = np.cos(th).astype(n.dtype), np.sin(th).astype(n.dtype)
     ns = geom.ns.astype(n.dtype)
     cos_tp = (ns * n).sum(axis=0)                       # cos(theta') = n_s . n
     nz_n = (n * n).sum(axis=0) > 0.0
@@ -349,8 +378,9 @@ def wetting(n, geom, params):
     out = n.copy()
     cands = []
     for sgn in (+1.0, -1.0):
-        a_s = math.cos(sgn * th) - math.sin(sgn * th) * cos_tp_s / sin_tp
-        a_n = math.sin(sgn * th) / sin_tp
+        # cos(+-theta) = cos(theta), sin(+-theta) = +-sin(theta)
+        a_s = cos_th - sgn * sin_th * cos_tp_s / sin_tp
+        a_n = sgn * sin_th / sin_tp
         cands.append(a_s * ns + a_n * n)
     d_plus = ((cands[0] - n) ** 2).sum(axis=0)
     d_minus = ((cands[1] - n) ** 2).sum(axis=0)

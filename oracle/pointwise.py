@@ -30,9 +30,10 @@ from .lattice import (
 
 
 class PointwiseStep:
-    def __init__(self, F, solid, params, reactive=None):
+    def __init__(self, F, solid, params, reactive=None, theta=None):
         self.F = np.asarray(F)   # any float dtype; every access converts to a Python float (FP64)
         self.solid = np.asarray(solid, dtype=bool)
+        self.theta = None if theta is None else np.asarray(theta, dtype=np.float64)   # per solid node, degrees
         self.p = params
         self.nz, self.ny, self.nx = self.solid.shape
         self.reactive = None if reactive is None else np.asarray(reactive, dtype=bool)
@@ -233,7 +234,7 @@ class PointwiseStep:
         if 1.0 - ct * ct < SIN2_EPS:
             return n
         st = math.sin(math.acos(max(-1.0, min(1.0, ct))))
-        th = math.radians(self.p.theta_deg)
+        th = math.radians(self.p.theta_deg if self.theta is None else self.wall_theta(s))
         best = None
         for sg in (1.0, -1.0):
             cand = [(math.cos(sg * th) - math.sin(sg * th) * ct / st) * ns[a] + math.sin(sg * th) / st * n[a]
@@ -242,6 +243,18 @@ class PointwiseStep:
             if best is None or d < best[0]:
                 best = (d, cand)
         return best[1]
+
+    def wall_theta(self, s):
+        """Weighted mean of the per-node contact angle over the solid D3Q19 neighbours of s."""
+        x, y, z = s
+        num = den = 0.0
+        for i in range(18):
+            c = C19L[i]
+            nb = self.site(x + c[0], y + c[1], z + c[2])
+            if self.is_solid(nb):
+                num += W19L[i] * float(self.theta[nb[2], nb[1], nb[0]])
+                den += W19L[i]
+        return num / den
 
     def curvature(self, s):
         x, y, z = s

@@ -322,6 +322,7 @@ def run_native(args):
 
     if not args.no_variants:
         variants["batched"] = measure_batched(lbm, torch, stream, world, max(args.steps // 10, 20), args.warmup)
+        variants["adjoint"] = measure_adjoint(lbm, torch, stream, world, 3000 if args.steps >= 1000 else 300)
 
     # end to end through the C ABI with host buffers: create from the host mask,
     # K x (step + read of the step's reaction sums), observables, destroy
@@ -433,6 +434,48 @@ def measure_batched(lbm, torch, stream, world, steps, warmup, seq_steps=20):
             "blocks": blocks, "sequential_value": round(v_s, 2), "speedup_vs_sequential": round(v_b / v_s, 3),
             "roofline": {"kernel": "k_main", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4)}}
+
+
+def measure_adjoint(lbm, torch, stream, world, nsteps):
+    """Gradient of the outlet conversion of the 96^3 column after nsteps steps with respect to
+    the per-solid-node contact angle and the inlet velocity: checkpointed forward
+    (ceil(sqrt(nsteps)) spacing) plus the reverse sweep, timed with CUDA events."""
+    from paper_2608_15781_b300.configs import WORKLOADS
+
+    wl = WORKLOADS["column96"]
+    solid = wl.mask()
+    N = int(solid.size)
+    L = lbm.Lattice(solid, wl.params, bc_z=wl.bc_z, stream=stream.cuda_stream)
+    L.step(200)                       # a developed inflow with gas at the reactive walls
+    f0 = L.get_state()
+    nf = L.info()["n_fluid"]
+    L.set_state(f0)                   # warm-up of both phases (allocates the checkpoints)
+    L.adjoint_forward(min(nsteps, 100))
+    L.adjoint_backward()
+    L.set_state(f0)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    J = L.adjoint_forward(nsteps)
+    e1.record(stream)
+    dth, du, _ = L.adjoint_backward()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    t_f, t_b = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    K = int(np.ceil(np.sqrt(nsteps)))
+    nstate = (nsteps + K - 1) // K + K + 3
+    # reverse sweep per step and fluid node: recompute step (361 B) + adjoint step
+    # (read f_t and lambda_{t+1}, write lambda_t: 3 x 180 B)
+    rev_bytes = nf * (361 + 540) * nsteps
+    peak, _ = measured_peaks()
+    L.close()
+    return {"value": round(world * N * nsteps / ((t_f + t_b) * 1e-3) / 1e6, 2), "unit": "MLUPS (forward+backward)",
+            "workload": f"column96 (96^3, shell 6, porosity 0.5, u_in 0.004, k 2e-3), {nf} fluid, after 200 steps",
+            "steps": nsteps, "checkpoint_every": K, "checkpoint_states": nstate,
+            "ms_forward": round(t_f, 2), "ms_backward": round(t_b, 2), "objective": J,
+            "dJ_du_in": du, "max_abs_dJ_dtheta_deg": float(np.abs(dth).max()),
+            "reverse_effective_gbs": round(rev_bytes / (t_b * 1e-3) / 1e9, 1),
+            "reverse_frac_of_peak": round(rev_bytes / (t_b * 1e-3) / 1e9 / peak, 4)}
 
 
 def main():

@@ -69,6 +69,11 @@ typedef struct {
   int32_t bc_z;              /* 0: periodic in z (paper, Sec. 2.2);
                                 1: velocity inlet at z=0, pressure outlet at z=nz-1
                                 (added by this library); x and y always periodic  */
+  const float *theta_deg;    /* host, optional nx*ny*nz contact angles in degrees,
+                                read at solid nodes; a wall node uses the D3Q19-
+                                weighted mean over its solid neighbours (a spatial
+                                wettability field, which the paper keeps uniform).
+                                NULL = lbm_params.theta_deg everywhere             */
 } lbm_geometry;
 
 typedef struct {
@@ -175,6 +180,50 @@ int lbm_tune(lbm_ctx *ctx, int32_t *blocks);
  * device bytes held.  Any pointer may be NULL. */
 int lbm_info(lbm_ctx *ctx, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd,
              int64_t *device_bytes);
+
+/* Replace the contact-angle field (host, nx*ny*nz degrees read at solid nodes,
+ * as lbm_geometry.theta_deg; NULL = the uniform params.theta_deg).  Synchronous;
+ * LBM_EINVAL for a non-finite value. */
+int lbm_set_wetting(lbm_ctx *ctx, const float *theta_deg);
+
+/* Column mode: set the inlet velocity and concentration (rewrites the inlet
+ * ghost plane, Eq. of the inlet reading: f^r = f^eq(1, u_in z), g = g^eq(c_in,
+ * u_in z)).  LBM_EINVAL in a periodic box. */
+int lbm_set_inlet(lbm_ctx *ctx, double u_in, double c_in);
+
+/* ---------------------------------------------------------------------------
+ * Reverse mode (discrete adjoint) of the outlet conversion of a column
+ *
+ *   J = 1 - Phi_out / Phi_in,  Phi = sum over the fluid nodes of plane z = 0
+ *   (in) or z = nz - 1 (out) of u_z C,  u_z = j_z / rho of the stored state,
+ *
+ * after nsteps steps from the current state, differentiated with respect to the
+ * per-solid-node contact angle (lbm_geometry.theta_deg) and the inlet velocity;
+ * the start state is held fixed.  The paper's coating discussion (Sec. 5.2)
+ * turns on how the wettability controls the conversion; this is its gradient.
+ * Branch decisions of the forward (interface thresholds, the n_+/n_- choice,
+ * the reaction clamps) are frozen.  Column mode, reaction_mode 0, FP32 storage
+ * only (else LBM_EINVAL).
+ *
+ * lbm_adjoint_forward advances the state by nsteps exactly as lbm_step does,
+ * storing a checkpoint every checkpoint_every steps (<= 0: ceil(sqrt(nsteps))),
+ * and returns J in *objective (may be NULL).  Device memory for about
+ * nsteps / K + K + 3 population states (K = checkpoint spacing) is allocated on
+ * first use and kept until lbm_destroy.  LBM_ENAN if Phi_in is zero or the
+ * fluxes are not finite.
+ *
+ * lbm_adjoint_backward (valid until the state changes) recomputes each segment
+ * from its checkpoint and runs the adjoint steps backwards.  Outputs, each
+ * multiplied by seed (dL/dJ of an enclosing objective; 1 for dJ):
+ *   dtheta_deg  host, nx*ny*nz doubles: dJ/dtheta per solid node, per degree
+ *               (0 at fluid nodes and at solids without a wall neighbour)
+ *   du_in       dJ/du_in
+ *   dstate      host, 45*N floats in the lbm_get_state layout: dJ/df of the
+ *               start state (state_bytes must equal 45 * N * sizeof(float))
+ * Any output may be NULL.  Overwrites the LBM_FIELD_* buffers of the last step. */
+int lbm_adjoint_forward(lbm_ctx *ctx, int64_t nsteps, int64_t checkpoint_every, double *objective);
+int lbm_adjoint_backward(lbm_ctx *ctx, double seed, double *dtheta_deg, double *du_in, float *dstate,
+                         size_t state_bytes);
 
 /* Release every device resource of the context; NULL is ignored. */
 void lbm_destroy(lbm_ctx *ctx);

@@ -14,6 +14,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "cglbm.h"
 #include "compact.cuh"
 #include "kernels.cuh"
@@ -69,6 +70,20 @@ struct Batch {
   std::vector<int> ev_kind;
   size_t ev_used = 0;
   bool profiling = false;
+  // reverse mode (lbm_adjoint_forward / lbm_adjoint_backward)
+  struct Adj {
+    std::vector<float *> cp;      // checkpoints f_{sK}, s = 0 .. nseg - 1
+    std::vector<float *> store;   // the states of one segment, recomputed
+    float *lam0 = nullptr, *lam1 = nullptr, *fbar = nullptr;   // slot-space adjoints
+    float *hbar = nullptr, *rho = nullptr, *rnbar = nullptr;   // dense per-node fields
+    float4 *nbar = nullptr;
+    float2 *coef = nullptr;
+    double *thbar = nullptr, *uin = nullptr;
+    size_t bytes = 0;
+    int64_t nsteps = 0, K = 0, nseg = 0, end_step = -1;
+    double phi_in = 0.0, phi_out = 0.0;
+    bool ready = false;
+  } adj;
 };
 
 }  // namespace
@@ -136,6 +151,12 @@ void free_all(Batch &b) {
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
   b.ev.clear();
+  Batch::Adj &a = b.adj;
+  for (float *p : a.cp) cudaFree(p);
+  for (float *p : a.store) cudaFree(p);
+  void *aptrs[] = {a.lam0, a.lam1, a.fbar, a.hbar, a.rho, a.rnbar, a.nbar, a.coef, a.thbar, a.uin};
+  for (void *p : aptrs) cudaFree(p);
+  a = Batch::Adj{};
 }
 
 int check_params(const lbm_params *p) {
@@ -161,14 +182,13 @@ int check_geometry(const lbm_geometry *g) {
   return LBM_OK;
 }
 
+float theta_rad(const lbm_params &p) { return (float)(p.theta_deg * 3.14159265358979323846 / 180.0); }
+
 StepParams make_step_params(const lbm_params &p) {
   StepParams s{};
   s.omega_cm = (float)(1.0 - 1.0 / p.tau);
   s.half_sigma = (float)(0.5 * p.sigma);
   s.beta = (float)p.beta;
-  const double th = p.theta_deg * 3.14159265358979323846 / 180.0;
-  s.cos_th = (float)std::cos(th);
-  s.sin_th = (float)std::sin(th);
   s.ax = (float)p.accel[0];
   s.ay = (float)p.accel[1];
   s.az = (float)p.accel[2];
@@ -287,7 +307,8 @@ void launch_solids(const Batch &b, cudaStream_t st, bool colour) {
 }
 
 // the kernels of one step (in -> out), on stream st
-void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int slot, bool prof) {
+void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int slot, bool prof,
+                  double *acc = nullptr) {
   auto pb = [&](int k) { if (prof) prof_begin(b, k, st); };
   auto pe = [&]() { if (prof) prof_end(b, st); };
   with_storage(b, [&](auto *tag) {
@@ -309,7 +330,7 @@ void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int sl
       pe();
     }
     pb(4);
-    launch_main<T>(b, st, fin, fout, b.acc, slot);
+    launch_main<T>(b, st, fin, fout, acc ? acc : b.acc, slot);
     pe();
   });
 }
@@ -498,12 +519,15 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   {
     // geometry kernels, one instance at a time (one-time set-up)
     uint8_t *d_solid = nullptr, *d_react = nullptr;
+    float *d_theta = nullptr;
     long long maxn = 0;
     for (int k = 0; k < n; ++k) maxn = std::max(maxn, b.h[k].d.L.n);
-    if (cudaMalloc((void **)&d_solid, maxn) != cudaSuccess || cudaMalloc((void **)&d_react, maxn) != cudaSuccess) {
+    if (cudaMalloc((void **)&d_solid, maxn) != cudaSuccess || cudaMalloc((void **)&d_react, maxn) != cudaSuccess ||
+        cudaMalloc((void **)&d_theta, maxn * sizeof(float)) != cudaSuccess) {
       (void)cudaGetLastError();
       cudaFree(d_solid);
       cudaFree(d_react);
+      cudaFree(d_theta);
       return LBM_ENOMEM;
     }
     for (int k = 0; k < n && rc == LBM_OK; ++k) {
@@ -514,11 +538,21 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
         break;
       }
       k_geom<<<node_grid(L), node_block(), 0, b.stream>>>(L, d_solid, geoms[k].reactive ? d_react : nullptr,
-                                                          b.link + b.h[k].d.node_off, b.nsv + b.h[k].d.node_off);
+                                                          theta_rad(params[k]), b.link + b.h[k].d.node_off,
+                                                          b.nsv + b.h[k].d.node_off);
+      if (geoms[k].theta_deg) {
+        if (cudaMemcpy(d_theta, geoms[k].theta_deg, L.n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+          rc = LBM_ECUDA;
+          break;
+        }
+        k_wall_theta<<<node_grid(L), node_block(), 0, b.stream>>>(L, b.link + b.h[k].d.node_off, d_theta,
+                                                                  theta_rad(params[k]), b.nsv + b.h[k].d.node_off);
+      }
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(b.stream) != cudaSuccess) rc = LBM_ECUDA;
     }
     cudaFree(d_solid);
     cudaFree(d_react);
+    cudaFree(d_theta);
     if (rc) return cuda_fail(b, cudaErrorUnknown);
     CK(cudaMemcpy(hlink.data(), b.link, nodes * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   }
@@ -652,22 +686,17 @@ int init_fields(Batch &b, int k, const float *rho_r, const float *rho_p, const f
   return rc;
 }
 
-int get_state(Batch &b, int k, float *dst, size_t bytes) {
-  if (!dst || k < 0 || k >= b.n) return LBM_EINVAL;
+// slot-space populations src (storage type T) of instance k -> host [45][n], zero at solids
+template <typename T>
+int slots_to_host(Batch &b, int k, const T *src, float *dst, size_t bytes) {
   const InstHost &ih = b.h[k];
-  if (bytes != (size_t)NPOP * ih.d.L.n * sizeof(float)) return LBM_EINVAL;
-  if (b.sticky) return b.sticky;
-  cudaSetDevice(b.device);
   const size_t nf = (size_t)ih.d.nf;
   float *d = nullptr;
   if (cudaMalloc((void **)&d, (size_t)NPOP * nf * sizeof(float)) != cudaSuccess) {
     (void)cudaGetLastError();
     return LBM_ENOMEM;
   }
-  with_storage(b, [&](auto *tag) {
-    using T = std::remove_pointer_t<decltype(tag)>;
-    k_slots_to_f32<T><<<(unsigned)((nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, (const T *)b.fa, d);
-  });
+  k_slots_to_f32<T><<<(unsigned)((nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, src, d);
   std::vector<float> h((size_t)NPOP * nf);
   cudaError_t e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(float), cudaMemcpyDeviceToHost, b.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b.stream);
@@ -681,6 +710,19 @@ int get_state(Batch &b, int k, float *dst, size_t bytes) {
     for (size_t t = 0; t < nf; ++t) o[ih.slot_node[t]] = s[t];
   }
   return LBM_OK;
+}
+
+int get_state(Batch &b, int k, float *dst, size_t bytes) {
+  if (!dst || k < 0 || k >= b.n) return LBM_EINVAL;
+  if (bytes != (size_t)NPOP * b.h[k].d.L.n * sizeof(float)) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  int rc = LBM_OK;
+  with_storage(b, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    rc = slots_to_host<T>(b, k, (const T *)b.fa, dst, bytes);
+  });
+  return rc;
 }
 
 int set_state(Batch &b, int k, const float *src, size_t bytes) {
@@ -887,6 +929,204 @@ int profile_read(Batch &b, double *ms, int64_t *launches, int32_t n) {
   return LBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// wettability field and inlet (parameters of the adjoint)
+// ---------------------------------------------------------------------------
+int set_wetting(Batch &b, int k, const float *theta_deg) {
+  if (k < 0 || k >= b.n) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const InstHost &ih = b.h[k];
+  const Lattice &L = ih.d.L;
+  float *d = nullptr;
+  if (theta_deg) {
+    for (long long i = 0; i < L.n; ++i)
+      if (!std::isfinite(theta_deg[i])) return LBM_EINVAL;
+    if (cudaMalloc((void **)&d, L.n * sizeof(float)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return LBM_ENOMEM;
+    }
+    if (cudaMemcpyAsync(d, theta_deg, L.n * sizeof(float), cudaMemcpyHostToDevice, b.stream) != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(b, cudaErrorUnknown);
+    }
+  }
+  k_wall_theta<<<node_grid(L), node_block(), 0, b.stream>>>(L, b.link + ih.d.node_off, d, theta_rad(ih.prm),
+                                                            b.nsv + ih.d.node_off);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b.stream);
+  cudaFree(d);
+  b.adj.ready = false;
+  return cuda_fail(b, e);
+}
+
+int set_inlet(Batch &b, int k, double u_in, double c_in) {
+  if (k < 0 || k >= b.n || !std::isfinite(u_in) || !std::isfinite(c_in)) return LBM_EINVAL;
+  InstHost &ih = b.h[k];
+  if (ih.d.L.bc_z != 1) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  ih.prm.u_in = u_in;
+  ih.prm.c_in = c_in;
+  const Inst &I = ih.d;
+  const dim3 blk(32, 4, 1), grd((I.L.nx + 31) / 32, (I.L.ny + 3) / 4, 1);
+  with_storage(b, [&](auto *tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    k_ghost_init_c<T><<<grd, blk, 0, b.stream>>>(I, b.ns, b.gidx, (float)u_in, (float)c_in, (float)ih.prm.rho_out,
+                                                  (T *)b.fa, (T *)b.fb);
+  });
+  CK(cudaGetLastError());
+  b.adj.ready = false;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reverse mode: checkpointed forward, then one adjoint step per forward step
+// ---------------------------------------------------------------------------
+int adj_alloc(Batch &b, int64_t nseg, int64_t K) {
+  Batch::Adj &a = b.adj;
+  const size_t sb = (size_t)NPOP * b.ns * sizeof(float);
+  const size_t nodes = (size_t)b.nodes;
+  auto grab = [&](void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
+      (void)cudaGetLastError();
+      return false;
+    }
+    a.bytes += bytes;
+    return true;
+  };
+  if (!a.lam0) {
+    bool ok = grab((void **)&a.lam0, sb) && grab((void **)&a.lam1, sb) && grab((void **)&a.fbar, sb) &&
+              grab((void **)&a.hbar, nodes * sizeof(float)) && grab((void **)&a.rho, nodes * sizeof(float)) &&
+              grab((void **)&a.rnbar, nodes * sizeof(float)) && grab((void **)&a.nbar, nodes * sizeof(float4)) &&
+              grab((void **)&a.coef, nodes * sizeof(float2)) && grab((void **)&a.thbar, nodes * sizeof(double)) &&
+              grab((void **)&a.uin, sizeof(double));
+    if (!ok) return LBM_ENOMEM;
+  }
+  while ((int64_t)a.cp.size() < nseg) {
+    float *p = nullptr;
+    if (!grab((void **)&p, sb)) return LBM_ENOMEM;
+    a.cp.push_back(p);
+  }
+  while ((int64_t)a.store.size() < K) {
+    float *p = nullptr;
+    if (!grab((void **)&p, sb)) return LBM_ENOMEM;
+    a.store.push_back(p);
+  }
+  return LBM_OK;
+}
+
+int adjoint_forward(Batch &b, int64_t nsteps, int64_t every, double *objective) {
+  if (b.n != 1 || b.half || nsteps < 1) return LBM_EINVAL;
+  const InstHost &ih = b.h[0];
+  if (ih.d.L.bc_z != 1 || ih.prm.reaction_mode != 0) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  Batch::Adj &a = b.adj;
+  a.ready = false;
+  int64_t K = every > 0 ? every : (int64_t)std::ceil(std::sqrt((double)nsteps));
+  K = std::max<int64_t>(1, std::min(K, nsteps));
+  const int64_t nseg = (nsteps + K - 1) / K;
+  int rc = adj_alloc(b, nseg, K);
+  if (rc) return rc;
+  const size_t sb = (size_t)NPOP * b.ns * sizeof(float);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if (s % K == 0) CK(cudaMemcpyAsync(a.cp[s / K], b.fa, sb, cudaMemcpyDeviceToDevice, b.stream));
+    rc = step_n(b, 1);
+    if (rc) return rc;
+  }
+  rc = launch_observables(b);
+  if (rc) return rc;
+  double h[8];
+  CK(cudaMemcpyAsync(h, b.obs, sizeof(h), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
+  if (!(h[4] != 0.0) || !std::isfinite(h[4]) || !std::isfinite(h[5])) return LBM_ENAN;
+  a.phi_in = h[4];
+  a.phi_out = h[5];
+  a.nsteps = nsteps;
+  a.K = K;
+  a.nseg = nseg;
+  a.end_step = b.step;
+  a.ready = true;
+  if (objective) *objective = 1.0 - a.phi_out / a.phi_in;
+  return LBM_OK;
+}
+
+// lambda_t from lambda_{t+1} (lam_in) and the state f_t
+int reverse_step(Batch &b, const float *ft, const float *lam_in, float *lam_out) {
+  Batch::Adj &a = b.adj;
+  const cudaStream_t st = b.stream;
+  const Slots S = slots(b);
+  const Inst &I = b.h[0].d;
+  const unsigned g128 = (unsigned)((S.nslots + 127) / 128), g256 = (unsigned)((S.nslots + 255) / 256);
+  const unsigned gb = (unsigned)((b.n_bnd + 255) / 256);
+  // forward quantities of step t
+  launch_density<float>(b, st, ft);
+  if (b.n_bnd > 0) launch_solids(b, st, true);
+  launch_normal(b, st);
+  if (b.n_bnd > 0) launch_solids(b, st, false);
+  CK(cudaMemsetAsync(a.nbar, 0, (size_t)b.nodes * sizeof(float4), st));
+  CK(cudaMemsetAsync(a.rnbar, 0, (size_t)b.nodes * sizeof(float), st));
+  k_adj_collide<<<g128, 128, 0, st>>>(S, I, ft, b.gidx, b.link, b.nrm, lam_in, a.fbar, a.nbar, a.hbar, a.rho);
+  k_adj_curv<<<g256, 256, 0, st>>>(S, I, b.nrm, a.hbar, a.nbar);
+  if (b.n_bnd > 0) k_adj_nsolid<<<gb, 256, 0, st>>>(I, b.bnd, b.n_bnd, b.link, b.nrm, a.nbar);
+  k_adj_normal<<<g256, 256, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, a.nbar, a.rnbar, a.thbar);
+  if (b.n_bnd > 0) k_adj_csolid<<<gb, 256, 0, st>>>(I, b.bnd, b.n_bnd, b.link, a.rnbar);
+  k_adj_coef<<<g256, 256, 0, st>>>(S, I, b.rhoN, a.rho, a.rnbar, a.coef);
+  const lbm_params &p = b.h[0].prm;
+  k_adj_pull<<<g256, 256, 0, st>>>(S, I, b.gidx, a.fbar, a.coef, (float)p.u_in, (float)p.c_in, lam_out, a.uin);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+int adjoint_backward(Batch &b, double seed, double *dtheta, double *du_in, float *dstate, size_t state_bytes) {
+  Batch::Adj &a = b.adj;
+  if (!a.ready || b.step != a.end_step || !std::isfinite(seed)) return LBM_EINVAL;
+  const InstHost &ih = b.h[0];
+  if (dstate && state_bytes != (size_t)NPOP * ih.d.L.n * sizeof(float)) return LBM_EINVAL;
+  if (b.sticky) return b.sticky;
+  cudaSetDevice(b.device);
+  const size_t sb = (size_t)NPOP * b.ns * sizeof(float);
+  // the recompute buffers take the constant ghost planes of the current state
+  for (int64_t j = 0; j < a.K; ++j) CK(cudaMemcpyAsync(a.store[j], b.fa, sb, cudaMemcpyDeviceToDevice, b.stream));
+  CK(cudaMemsetAsync(a.thbar, 0, (size_t)b.nodes * sizeof(double), b.stream));
+  CK(cudaMemsetAsync(a.uin, 0, sizeof(double), b.stream));
+  const double a_in = seed * a.phi_out / (a.phi_in * a.phi_in), a_out = -seed / a.phi_in;
+  const Slots S = slots(b);
+  k_adj_seed<<<(unsigned)((S.nslots + 255) / 256), 256, 0, b.stream>>>(S, ih.d, (const float *)b.fa, (float)a_in,
+                                                                       (float)a_out, a.lam0);
+  CK(cudaGetLastError());
+  float *lam = a.lam0, *lamn = a.lam1;
+  for (int64_t s = a.nseg - 1; s >= 0; --s) {
+    const int64_t t0 = s * a.K, t1 = std::min(t0 + a.K, a.nsteps);
+    CK(cudaMemcpyAsync(a.store[0], a.cp[s], sb, cudaMemcpyDeviceToDevice, b.stream));
+    for (int64_t t = t0 + 1; t < t1; ++t)
+      enqueue_step(b, b.stream, a.store[t - 1 - t0], a.store[t - t0], 0, false, b.acc_scratch);
+    CK(cudaGetLastError());
+    for (int64_t t = t1 - 1; t >= t0; --t) {
+      const int rc = reverse_step(b, a.store[t - t0], lam, lamn);
+      if (rc) return rc;
+      std::swap(lam, lamn);
+    }
+  }
+  // the step kernels left rho^N and the normals of an early step in the dense fields
+  if (dtheta) {
+    CK(cudaMemcpyAsync(dtheta, a.thbar, (size_t)ih.d.L.n * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  }
+  double u = 0.0;
+  CK(cudaMemcpyAsync(&u, a.uin, sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
+  if (du_in) *du_in = u;
+  if (dstate) {
+    k_adj_ghost0<<<(unsigned)((S.nslots + 255) / 256), 256, 0, b.stream>>>(S, ih.d, a.cp[0], lam);
+    CK(cudaGetLastError());
+    const int rc = slots_to_host<float>(b, 0, lam, dstate, state_bytes);
+    if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1059,6 +1299,19 @@ int lbm_info(lbm_ctx *c, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd
   return LBM_OK;
 }
 
+int lbm_set_wetting(lbm_ctx *c, const float *theta_deg) { return c ? set_wetting(c->b, 0, theta_deg) : LBM_EINVAL; }
+
+int lbm_set_inlet(lbm_ctx *c, double u_in, double c_in) { return c ? set_inlet(c->b, 0, u_in, c_in) : LBM_EINVAL; }
+
+int lbm_adjoint_forward(lbm_ctx *c, int64_t nsteps, int64_t checkpoint_every, double *objective) {
+  return c ? adjoint_forward(c->b, nsteps, checkpoint_every, objective) : LBM_EINVAL;
+}
+
+int lbm_adjoint_backward(lbm_ctx *c, double seed, double *dtheta_deg, double *du_in, float *dstate,
+                         size_t state_bytes) {
+  return c ? adjoint_backward(c->b, seed, dtheta_deg, du_in, dstate, state_bytes) : LBM_EINVAL;
+}
+
 void lbm_destroy(lbm_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->b.device);
@@ -1150,7 +1403,7 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   float *fout = f_out - L.plane;
   const dim3 nb = node_block(), ng = node_grid(L);
   if (cudaMemsetAsync(acc, 0, 4 * sizeof(double), st) != cudaSuccess) return LBM_ECUDA;
-  k_geom<<<ng, nb, 0, st>>>(L, solid, reactive, link, ns);
+  k_geom<<<ng, nb, 0, st>>>(L, solid, reactive, theta_rad(*params), link, ns);
   k_density<<<ng, nb, 0, st>>>(L, fin, link, rhoN);
   k_color_solid_all<<<ng, nb, 0, st>>>(L, link, rhoN);
   k_normal<<<ng, nb, 0, st>>>(L, sp, rhoN, link, ns, nrm);

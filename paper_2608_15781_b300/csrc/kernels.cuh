@@ -23,7 +23,6 @@ struct StepParams {
   float omega_cm;     // 1 - 1/tau (Eq. post_collision_moments)
   float half_sigma;   // sigma / 2 (Eq. continuum_surface_force)
   float beta;
-  float cos_th, sin_th;
   float ax, ay, az;
   float inv_tau_g;    // 1 / (D / c_s^2 + 1/2), c_s^2 = 1/4 on D3Q7
   float k_rate, xi, rho_out;
@@ -202,8 +201,11 @@ __device__ __forceinline__ bool solid_at(const Lattice &L, const uint8_t *__rest
   return solid[nidx(L, x, y, z)] != 0;
 }
 
+// ns[node].w of a wall node holds its contact angle theta in radians: the
+// uniform value theta_rad, or the D3Q19-weighted mean of a per-solid-node field
+// (k_wall_theta).  k_geom writes the uniform value.
 __global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8_t *__restrict__ reactive,
-                       uint32_t *__restrict__ link, float4 *__restrict__ ns) {
+                       float theta_rad, uint32_t *__restrict__ link, float4 *__restrict__ ns) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -250,12 +252,43 @@ __global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8
       const float m = sqrtf(sx * sx + sy * sy + sz * sz);
       if (m > 0.f) {
         bits |= BIT_NS_OK;
-        nsv = make_float4(sx / m, sy / m, sz / m, 0.f);
+        nsv = make_float4(sx / m, sy / m, sz / m, theta_rad);
       }
     }
   }
   link[node] = bits;
   ns[node] = nsv;
+}
+
+// Contact angle of every wall node from a per-node field theta_deg (degrees, read
+// at solid nodes): the D3Q19-weighted mean over the solid neighbours x + c_i of
+// the geometry stencil (a spatially varying wettability; the paper's is uniform).
+// theta_deg null: the uniform value theta_rad.
+__global__ void k_wall_theta(Lattice L, const uint32_t *__restrict__ link, const float *__restrict__ theta_deg,
+                             float theta_rad, float4 *__restrict__ ns) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const long long node = nidx(L, x, y, z);
+  const uint32_t lk = link[node];
+  if ((lk & BIT_SOLID) || !(lk & BIT_WALL) || !(lk & BIT_NS_OK)) return;
+  float th = theta_rad;
+  if (theta_deg) {
+    float num = 0.f, den = 0.f;
+    for (int i = 0; i < Q - 1; ++i) {
+      const int xx = ((x + CX[i]) % L.nx + L.nx) % L.nx, yy = ((y + CY[i]) % L.ny + L.ny) % L.ny;
+      int zz = z + CZ[i];
+      zz = L.bc_z == 0 ? (zz + L.nz) % L.nz : (zz < 0 ? 0 : (zz >= L.nz ? L.nz - 1 : zz));
+      const long long nb = nidx(L, xx, yy, zz);
+      if (link[nb] & BIT_SOLID) {
+        num += W[i] * theta_deg[nb];
+        den += W[i];
+      }
+    }
+    th = num / den * 0.017453292519943295f;
+  }
+  ns[node].w = th;
 }
 
 // ---------------------------------------------------------------------------
@@ -414,18 +447,20 @@ __device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk
     nz_ = gz * inv;
     if ((lk & BIT_WALL) && (lk & BIT_NS_OK)) {
       const float4 s = ns[node];
+      float sin_th, cos_th;
+      sincosf(s.w, &sin_th, &cos_th);
       const float c = s.x * nx_ + s.y * ny_ + s.z * nz_;          // cos(theta')
       const float tx = nx_ - c * s.x, ty = ny_ - c * s.y, tz = nz_ - c * s.z;
       const float st2 = tx * tx + ty * ty + tz * tz;              // sin^2(theta')
       if (st2 >= SIN2_EPS) {
         const float st = sqrtf(st2);
-        const float a_s = P.sin_th * c / st, a_n = P.sin_th / st;
-        const float px = (P.cos_th - a_s) * s.x + a_n * nx_;
-        const float py = (P.cos_th - a_s) * s.y + a_n * ny_;
-        const float pz = (P.cos_th - a_s) * s.z + a_n * nz_;
-        const float mx = (P.cos_th + a_s) * s.x - a_n * nx_;
-        const float my = (P.cos_th + a_s) * s.y - a_n * ny_;
-        const float mz = (P.cos_th + a_s) * s.z - a_n * nz_;
+        const float a_s = sin_th * c / st, a_n = sin_th / st;
+        const float px = (cos_th - a_s) * s.x + a_n * nx_;
+        const float py = (cos_th - a_s) * s.y + a_n * ny_;
+        const float pz = (cos_th - a_s) * s.z + a_n * nz_;
+        const float mx = (cos_th + a_s) * s.x - a_n * nx_;
+        const float my = (cos_th + a_s) * s.y - a_n * ny_;
+        const float mz = (cos_th + a_s) * s.z - a_n * nz_;
         const float dp = (px - nx_) * (px - nx_) + (py - ny_) * (py - ny_) + (pz - nz_) * (pz - nz_);
         const float dm = (mx - nx_) * (mx - nx_) + (my - ny_) * (my - ny_) + (mz - nz_) * (mz - nz_);
         if (dp <= dm) {

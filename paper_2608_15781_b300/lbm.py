@@ -33,7 +33,7 @@ SYMBOLS = (
     "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static", "lbm_tune",
     "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables", "lbm_batch_get_state",
     "lbm_batch_set_state", "lbm_batch_tune", "lbm_batch_profile", "lbm_batch_profile_read",
-    "lbm_batch_destroy",
+    "lbm_batch_destroy", "lbm_set_wetting", "lbm_set_inlet", "lbm_adjoint_forward", "lbm_adjoint_backward",
 )
 STATIC_MAX_NODES = 131072   # LBM_STATIC_MAX_NODES
 
@@ -47,7 +47,8 @@ class LbmError(RuntimeError):
 
 class _Geometry(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("solid", ctypes.c_void_p), ("reactive", ctypes.c_void_p), ("bc_z", ctypes.c_int32)]
+                ("solid", ctypes.c_void_p), ("reactive", ctypes.c_void_p), ("bc_z", ctypes.c_int32),
+                ("theta_deg", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -134,6 +135,10 @@ def load_library(path=LIB_PATH):
         "lbm_batch_profile": (ctypes.c_int, [P, I32]),
         "lbm_batch_profile_read": (ctypes.c_int, [P, P, P, I32]),
         "lbm_batch_destroy": (None, [P]),
+        "lbm_set_wetting": (ctypes.c_int, [P, P]),
+        "lbm_set_inlet": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double]),
+        "lbm_adjoint_forward": (ctypes.c_int, [P, I64, I64, P]),
+        "lbm_adjoint_backward": (ctypes.c_int, [P, ctypes.c_double, P, P, P, SZ]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -157,17 +162,12 @@ def _ptr(a):
 
 
 # --------------------------------------------------------------------------- C-named calls
-def lbm_create(solid, params, reactive=None, bc_z=0, stream=None):
-    """Create a context for the (nz, ny, nx) mask ``solid``; returns the opaque handle."""
+def lbm_create(solid, params, reactive=None, bc_z=0, stream=None, theta=None):
+    """Create a context for the (nz, ny, nx) mask ``solid``; returns the opaque handle.
+
+    ``theta``: optional (nz, ny, nx) contact angles in degrees, read at solid nodes."""
     lib = load_library()
-    solid = np.ascontiguousarray(solid, dtype=np.uint8)
-    if solid.ndim != 3:
-        raise LbmError(LBM_EINVAL, "solid must be a (nz, ny, nx) array")
-    nz, ny, nx = solid.shape
-    react = None if reactive is None else np.ascontiguousarray(reactive, dtype=np.uint8)
-    if react is not None and react.shape != solid.shape:
-        raise LbmError(LBM_EINVAL, "reactive mask shape")
-    g = _Geometry(nx, ny, nz, solid.ctypes.data, react.ctypes.data if react is not None else None, int(bc_z))
+    g, _keep = _geometry(solid, reactive, bc_z, theta)
     p = params.to_c(stream)
     h = ctypes.c_void_p()
     _check(lib.lbm_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)), "lbm_create")
@@ -247,6 +247,35 @@ def lbm_tune(ctx):
     return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]))
 
 
+def lbm_set_wetting(ctx, theta):
+    """Replace the contact-angle field ((nz, ny, nx) degrees at solid nodes; None = uniform)."""
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+    _check(load_library().lbm_set_wetting(ctx, _ptr(th)), "lbm_set_wetting")
+
+
+def lbm_set_inlet(ctx, u_in, c_in):
+    _check(load_library().lbm_set_inlet(ctx, float(u_in), float(c_in)), "lbm_set_inlet")
+
+
+def lbm_adjoint_forward(ctx, nsteps, checkpoint_every=0):
+    """Advance nsteps storing checkpoints; returns the outlet conversion J."""
+    j = ctypes.c_double()
+    _check(load_library().lbm_adjoint_forward(ctx, int(nsteps), int(checkpoint_every), ctypes.byref(j)),
+           "lbm_adjoint_forward")
+    return j.value
+
+
+def lbm_adjoint_backward(ctx, shape, seed=1.0, want_state=False):
+    """(dJ/dtheta per node (degrees^-1, float64), dJ/du_in, dJ/df_0 or None), each times seed."""
+    nz, ny, nx = shape
+    dth = np.empty((nz, ny, nx), dtype=np.float64)
+    du = ctypes.c_double()
+    ds = np.empty((NPOP, nz, ny, nx), dtype=np.float32) if want_state else None
+    _check(load_library().lbm_adjoint_backward(ctx, float(seed), _ptr(dth), ctypes.byref(du), _ptr(ds),
+                                               ds.nbytes if ds is not None else 0), "lbm_adjoint_backward")
+    return dth, du.value, ds
+
+
 def lbm_destroy(ctx):
     if ctx is not None and ctx.value:
         load_library().lbm_destroy(ctx)
@@ -269,28 +298,34 @@ def lbm_step_static(shape, solid_dev, f_in_dev, f_out_dev, params, reactive_dev=
                                            delta_sum_dev, ctypes.byref(p)), "lbm_step_static")
 
 
-def _geometry(solid, reactive, bc_z):
+def _geometry(solid, reactive, bc_z, theta=None):
     solid = np.ascontiguousarray(solid, dtype=np.uint8)
     if solid.ndim != 3:
         raise LbmError(LBM_EINVAL, "solid must be a (nz, ny, nx) array")
     react = None if reactive is None else np.ascontiguousarray(reactive, dtype=np.uint8)
     if react is not None and react.shape != solid.shape:
         raise LbmError(LBM_EINVAL, "reactive mask shape")
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+    if th is not None and th.shape != solid.shape:
+        raise LbmError(LBM_EINVAL, "theta field shape")
     nz, ny, nx = solid.shape
-    g = _Geometry(nx, ny, nz, solid.ctypes.data, react.ctypes.data if react is not None else None, int(bc_z))
-    return g, (solid, react)
+    g = _Geometry(nx, ny, nz, solid.ctypes.data, react.ctypes.data if react is not None else None, int(bc_z),
+                  th.ctypes.data if th is not None else None)
+    return g, (solid, react, th)
 
 
-def lbm_batch_create(solids, params, reactives=None, bc_z=None, stream=None):
-    """Create a batch of independent lattices (lists of masks, Params, optional r masks, bc_z)."""
+def lbm_batch_create(solids, params, reactives=None, bc_z=None, stream=None, thetas=None):
+    """Create a batch of independent lattices (lists of masks, Params, optional r masks, bc_z,
+    optional contact-angle fields)."""
     lib = load_library()
     n = len(solids)
     reactives = reactives or [None] * n
+    thetas = thetas or [None] * n
     bc_z = bc_z if bc_z is not None else [0] * n
     geoms = (_Geometry * n)()
     keep = []
     for k in range(n):
-        g, arrays = _geometry(solids[k], reactives[k], bc_z[k])
+        g, arrays = _geometry(solids[k], reactives[k], bc_z[k], thetas[k])
         geoms[k] = g
         keep.append(arrays)
     prms = (_Params * n)(*[p.to_c(stream) for p in params])
@@ -303,11 +338,11 @@ def lbm_batch_create(solids, params, reactives=None, bc_z=None, stream=None):
 class Lattice:
     """One lattice on the current CUDA device, driven through the C ABI."""
 
-    def __init__(self, solid, params, reactive=None, bc_z=0, stream=None):
+    def __init__(self, solid, params, reactive=None, bc_z=0, stream=None, theta=None):
         self.shape = tuple(np.shape(solid))
         self.params = params
         self.bc_z = bc_z
-        self.ctx = lbm_create(solid, params, reactive=reactive, bc_z=bc_z, stream=stream)
+        self.ctx = lbm_create(solid, params, reactive=reactive, bc_z=bc_z, stream=stream, theta=theta)
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
@@ -344,6 +379,18 @@ class Lattice:
 
     def tune(self):
         return lbm_tune(self.ctx)
+
+    def set_wetting(self, theta):
+        lbm_set_wetting(self.ctx, theta)
+
+    def set_inlet(self, u_in, c_in=None):
+        lbm_set_inlet(self.ctx, u_in, self.params.c_in if c_in is None else c_in)
+
+    def adjoint_forward(self, nsteps, checkpoint_every=0):
+        return lbm_adjoint_forward(self.ctx, nsteps, checkpoint_every)
+
+    def adjoint_backward(self, seed=1.0, want_state=False):
+        return lbm_adjoint_backward(self.ctx, self.shape, seed, want_state)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

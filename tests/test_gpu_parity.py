@@ -130,6 +130,39 @@ def test_single_step_random_state(bc, mode, nx):
         assert abs(ob[k] - oo[k]) < 1e-5 * abs(oo[k]) + 1e-6, k
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+def test_single_step_contact_angle_field(bc):
+    """Per-solid-node contact angles (each wall node: weighted mean over its solid neighbours)."""
+    shape = (17, 15, 18)
+    rng = np.random.default_rng(40 + bc)
+    solid = rng.random(shape) < 0.3
+    theta = rng.uniform(20.0, 150.0, shape).astype(np.float32)
+    p = lbm.Params(sigma=0.05, theta_deg=60.0, k_rate=0.05, u_in=0.01, c_in=0.7)
+    op = _oparams(p, bc)
+    g = O.Geometry(solid=solid, bc_z=bc, theta_deg=theta.astype(np.float64))
+    rr, rp, conc, u, rng = _random_state(shape, solid, 8)
+    st = O.init_state(g, op, rho_r=rr, rho_p=rp, conc=conc, u=u)
+    st.f += 1e-3 * rng.standard_normal(st.f.shape)
+    st.f[:, g.solid] = 0.0
+    f32 = st.f.astype(np.float32)
+    st.f = f32.astype(np.float64)
+    with lbm.Lattice(solid, p, bc_z=bc, theta=theta) as L:
+        L.set_state(f32)
+        L.step(1)
+        out = L.get_state()
+        # set_wetting(None) returns to the uniform angle
+        L.set_wetting(None)
+        L.set_state(f32)
+        L.step(1)
+        out_u = L.get_state()
+    new = O.step(st, g, op)
+    err = np.abs(out.astype(np.float64) - new.f)[:, g.fluid]
+    assert err.max() < 5 * TOL_STEP_POP, err.max()
+    new_u = O.step(st, O.Geometry(solid=solid, bc_z=bc), op)
+    assert np.abs(out_u.astype(np.float64) - new_u.f)[:, g.fluid].max() < 5 * TOL_STEP_POP
+    assert np.abs(new_u.f - new.f).max() > 1e-4      # the field matters in this case
+
+
 # --------------------------------------------------------------------- trajectories
 def _run_with_checkpoints(L, nsteps, at):
     """Run nsteps on the GPU; at the steps in ``at`` keep (pre, post) states of that single step."""

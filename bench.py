@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",
                     help="population storage of the headline run (the other is reported under variants)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="T",
+                    help="only time the adjoint variant over T steps and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -248,9 +250,13 @@ def run_native(args):
     from paper_2608_15781_b300.configs import WORKLOADS
 
     build.build()
+    stream = torch.cuda.current_stream()
+    if args.adjoint_only:
+        if rank == 0:
+            print(json.dumps(measure_adjoint(lbm, torch, stream, world, args.adjoint_only)), flush=True)
+        return 0
     wl = WORKLOADS[args.workload]
     solid = wl.mask()
-    stream = torch.cuda.current_stream()
     N = wl.nodes
 
     def barrier():

@@ -481,9 +481,8 @@ __global__ void k_adj_curv(Slots S, const __grid_constant__ Inst I, const float4
     }
     const float cn = c[0] * nme.x + c[1] * nme.y + c[2] * nme.z;
     const float s = -w3 * Hb;
-    atomicAdd(&nbar[nb].x, s * (c[0] - cn * nme.x));
-    atomicAdd(&nbar[nb].y, s * (c[1] - cn * nme.y));
-    atomicAdd(&nbar[nb].z, s * (c[2] - cn * nme.z));
+    atomicAdd(&nbar[nb], make_float4(s * (c[0] - cn * nme.x), s * (c[1] - cn * nme.y), s * (c[2] - cn * nme.z),
+                                     0.f));
   }
   const float n3[3] = {nme.x, nme.y, nme.z};
   float o[3];
@@ -491,9 +490,7 @@ __global__ void k_adj_curv(Slots S, const __grid_constant__ Inst I, const float4
     o[a] = 0.f;
     for (int b = 0; b < 3; ++b) o[a] += (d[a][b] + d[b][a]) * n3[b];
   }
-  atomicAdd(&nbar[node].x, Hb * o[0]);
-  atomicAdd(&nbar[node].y, Hb * o[1]);
-  atomicAdd(&nbar[node].z, Hb * o[2]);
+  atomicAdd(&nbar[node], make_float4(Hb * o[0], Hb * o[1], Hb * o[2], 0.f));
 }
 
 // nsolid: n(s) = A / |A|, A = sum_i w_i n(s + c_i) over fluid neighbours
@@ -526,10 +523,7 @@ __global__ void k_adj_nsolid(const __grid_constant__ Inst I, const uint32_t *__r
   if (bx == 0.f && by == 0.f && bz == 0.f) return;
   for (int i = 0; i < Q - 1; ++i) {
     if ((lk >> i) & 1u) {
-      const unsigned nb = St.nb(CX[i], CY[i], CZ[i]);
-      atomicAdd(&nbar[nb].x, W[i] * bx);
-      atomicAdd(&nbar[nb].y, W[i] * by);
-      atomicAdd(&nbar[nb].z, W[i] * bz);
+      atomicAdd(&nbar[St.nb(CX[i], CY[i], CZ[i])], make_float4(W[i] * bx, W[i] * by, W[i] * bz, 0.f));
     }
   }
 }
@@ -663,67 +657,75 @@ __global__ void __launch_bounds__(256) k_adj_pull(Slots S, const __grid_constant
     const Lattice &L = I.L;
     const unsigned ns = (unsigned)S.ns;
     const uint32_t pk = S.node[t];
-    int x, y, z;
-    bool ghost = pk == kNoNode;
-    if (!ghost) {
+    if (pk != kNoNode) {
+      // fluid slot: the 19 destinations once (slot, or -1 solid, or -2 outside the column)
+      int x, y, z;
       unpack(pk, x, y, z);
-    } else {
-      const long long q = (long long)t - I.ghost;
-      z = q < L.plane ? -1 : L.nz;
-      const long long r = q < L.plane ? q : q - L.plane;
-      y = (int)(r / L.nx);
-      x = (int)(r % L.nx);
-    }
-    const bool inlet = ghost && z < 0;
-    const long long own_node = ghost ? 0 : nidx(L, x, y, z);
-    float lam_v[NPOP];
+      PullOffsets O;
+      O.init(L, x, y, z);
+      StencilOffsets St;
+      St.init(L, x, y, z);
+      int tgt[Q];
+      float2 cf[Q];
 #pragma unroll
-    for (int p = 0; p < NPOP; ++p) {
-      int d, po;   // velocity index and opposite population
-      if (p < 2 * Q) {
-        const int i = p % Q;
-        d = i;
-        po = p - i + OPP[i];
-      } else {
-        d = GDIR[p - 2 * Q];
-        po = 2 * Q + GOPP[p - 2 * Q];
+      for (int i = 0; i < Q; ++i) {
+        const int zt = z + CZ[i];
+        const bool inside = L.bc_z == 0 || (zt >= 0 && zt < L.nz);
+        tgt[i] = inside ? __ldg(gidx + O.src(-CX[i], -CY[i], -CZ[i])) : -2;
+        cf[i] = tgt[i] >= 0 ? coef[St.nb(CX[i], CY[i], CZ[i])] : make_float2(0.f, 0.f);
       }
-      int zt = z + CZ[d];
-      float v = 0.f;
-      bool inside = true;
-      if (L.bc_z == 1) {
-        inside = zt >= 0 && zt < L.nz;
-      } else {
-        zt = (zt + L.nz) % L.nz;
-      }
-      if (inside) {
-        const int xt = (x + CX[d] + L.nx) % L.nx, yt = (y + CY[d] + L.ny) % L.ny;
-        const int st = gidx[(long long)(zt + 1) * L.plane + (long long)yt * L.nx + xt];
-        if (st >= 0) {
-          v = fbar[(unsigned)p * ns + (unsigned)st];
-          if (p < 2 * Q) {
-            const float2 cf = coef[nidx(L, xt, yt, zt)];
-            v += p < Q ? cf.x : cf.y;
-          }
-        } else if (!ghost) {
+      const float2 co = coef[St.own];
+#pragma unroll
+      for (int p = 0; p < NPOP; ++p) {
+        int d, po;
+        if (p < 2 * Q) {
+          d = p % Q;
+          po = p - d + OPP[d];
+        } else {
+          d = GDIR[p - 2 * Q];
+          po = 2 * Q + GOPP[p - 2 * Q];
+        }
+        float v = 0.f;
+        if (tgt[d] >= 0) {
+          v = fbar[(unsigned)p * ns + (unsigned)tgt[d]];
+          if (p < Q) v += cf[d].x;
+          else if (p < 2 * Q) v += cf[d].y;
+        } else if (tgt[d] == -1) {
           v = fbar[(unsigned)po * ns + t];
-          if (po < 2 * Q) {
-            const float2 cf = coef[own_node];
-            v += po < Q ? cf.x : cf.y;
+          if (po < Q) v += co.x;
+          else if (po < 2 * Q) v += co.y;
+        }
+        lam[(unsigned)p * ns + t] = v;
+      }
+    } else {
+      // ghost slot (column mode): only the populations entering the column are used
+      const long long q = (long long)t - I.ghost;
+      const bool inlet = q < L.plane;
+      const int z = inlet ? -1 : L.nz;
+      const long long r = inlet ? q : q - L.plane;
+      const int y = (int)(r / L.nx), x = (int)(r % L.nx);
+      double s = 0.0;
+      for (int p = 0; p < NPOP; ++p) {
+        const int d = p < 2 * Q ? p % Q : GDIR[p - 2 * Q];
+        float v = 0.f;
+        if (CZ[d] == (inlet ? 1 : -1)) {
+          const int xt = (x + CX[d] + L.nx) % L.nx, yt = (y + CY[d] + L.ny) % L.ny, zt = z + CZ[d];
+          const int st = gidx[(long long)(zt + 1) * L.plane + (long long)yt * L.nx + xt];
+          if (st >= 0) {
+            v = fbar[(unsigned)p * ns + (unsigned)st];
+            if (p < 2 * Q) {
+              const float2 c2 = coef[nidx(L, xt, yt, zt)];
+              v += p < Q ? c2.x : c2.y;
+            }
           }
         }
+        lam[(unsigned)p * ns + t] = v;
+        // inlet ghost: f^r_i = f^eq_i(1, u_in z) for c_iz = 1, g_4 = w_4 c_in (1 + 4 u_in)
+        if (inlet && v != 0.f) {
+          if (p < Q) s += (double)v * (double)(W[p] * (3.0f + 6.0f * u_in));
+          if (p == 2 * Q + 4) s += (double)v * (double)(4.0f * W7[4] * c_in);
+        }
       }
-      lam_v[p] = v;
-    }
-#pragma unroll
-    for (int p = 0; p < NPOP; ++p) lam[(unsigned)p * ns + t] = lam_v[p];
-    if (inlet) {
-      // inlet ghost: f^r_i = f^eq_i(1, u_in z) for c_iz = 1, g_4 = w_4 c_in (1 + 4 u_in)
-      double s = 0.0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i)
-        if (CZ[i] == 1) s += (double)lam_v[i] * (double)(W[i] * (3.0f + 6.0f * u_in));
-      s += (double)lam_v[2 * Q + 4] * (double)(4.0f * W7[4] * c_in);
       du = s;
     }
   }

@@ -220,7 +220,8 @@ int lbm_set_inlet(lbm_ctx *ctx, double u_in, double c_in);
  *   du_in       dJ/du_in
  *   dstate      host, 45*N floats in the lbm_get_state layout: dJ/df of the
  *               start state (state_bytes must equal 45 * N * sizeof(float))
- * Any output may be NULL.  Overwrites the LBM_FIELD_* buffers of the last step. */
+ * Any output may be NULL.  The state and the LBM_FIELD_* buffers are left as the
+ * forward left them. */
 int lbm_adjoint_forward(lbm_ctx *ctx, int64_t nsteps, int64_t checkpoint_every, double *objective);
 int lbm_adjoint_backward(lbm_ctx *ctx, double seed, double *dtheta_deg, double *du_in, float *dstate,
                          size_t state_bytes);

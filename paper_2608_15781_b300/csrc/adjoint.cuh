@@ -389,7 +389,7 @@ __global__ void k_adj_seed(Slots S, const __grid_constant__ Inst I, const float 
 }
 
 // collide: local adjoint at every fluid slot
-__global__ void __launch_bounds__(128) k_adj_collide(Slots S, const __grid_constant__ Inst I,
+__global__ void __launch_bounds__(128, 3) k_adj_collide(Slots S, const __grid_constant__ Inst I,
                                                      const float *__restrict__ fin, const int *__restrict__ gidx,
                                                      const uint32_t *__restrict__ link,
                                                      const float4 *__restrict__ nrm, const float *__restrict__ lam,
@@ -665,16 +665,19 @@ __global__ void __launch_bounds__(256) k_adj_pull(Slots S, const __grid_constant
       O.init(L, x, y, z);
       StencilOffsets St;
       St.init(L, x, y, z);
+      // branch-free: every load is issued (the bounce-back and dropped cases read
+      // the node's own slot and are selected or zeroed afterwards)
       int tgt[Q];
       float2 cf[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int zt = z + CZ[i];
         const bool inside = L.bc_z == 0 || (zt >= 0 && zt < L.nz);
-        tgt[i] = inside ? __ldg(gidx + O.src(-CX[i], -CY[i], -CZ[i])) : -2;
-        cf[i] = tgt[i] >= 0 ? coef[St.nb(CX[i], CY[i], CZ[i])] : make_float2(0.f, 0.f);
+        const unsigned gi = inside ? O.src(-CX[i], -CY[i], -CZ[i]) : O.own;
+        const int s_ = __ldg(gidx + gi);
+        tgt[i] = inside ? s_ : -2;
+        cf[i] = __ldg(coef + (tgt[i] >= 0 ? St.nb(CX[i], CY[i], CZ[i]) : St.own));
       }
-      const float2 co = coef[St.own];
 #pragma unroll
       for (int p = 0; p < NPOP; ++p) {
         int d, po;
@@ -685,17 +688,14 @@ __global__ void __launch_bounds__(256) k_adj_pull(Slots S, const __grid_constant
           d = GDIR[p - 2 * Q];
           po = 2 * Q + GOPP[p - 2 * Q];
         }
-        float v = 0.f;
-        if (tgt[d] >= 0) {
-          v = fbar[(unsigned)p * ns + (unsigned)tgt[d]];
-          if (p < Q) v += cf[d].x;
-          else if (p < 2 * Q) v += cf[d].y;
-        } else if (tgt[d] == -1) {
-          v = fbar[(unsigned)po * ns + t];
-          if (po < Q) v += co.x;
-          else if (po < 2 * Q) v += co.y;
-        }
-        lam[(unsigned)p * ns + t] = v;
+        const bool pulled = tgt[d] >= 0;
+        const int pp = pulled ? p : po;
+        const unsigned addr = (unsigned)pp * ns + (pulled ? (unsigned)tgt[d] : t);
+        float v = __ldg(fbar + addr);
+        // coefficient of the destination node (its own coefficient for bounce-back)
+        if (pp < Q) v += cf[d].x;
+        else if (pp < 2 * Q) v += cf[d].y;
+        lam[(unsigned)p * ns + t] = tgt[d] == -2 ? 0.f : v;
       }
     } else {
       // ghost slot (column mode): only the populations entering the column are used

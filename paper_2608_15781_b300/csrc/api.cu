@@ -74,6 +74,8 @@ struct Batch {
   struct Adj {
     std::vector<float *> cp;      // checkpoints f_{sK}, s = 0 .. nseg - 1
     std::vector<float *> store;   // the states of one segment, recomputed
+    std::vector<float *> seg_rhoN;     // rho^N of each state of the segment (dense)
+    std::vector<float4 *> seg_nrm;     // wetted normals and |grad rho^N| of each state
     float *lam0 = nullptr, *lam1 = nullptr, *fbar = nullptr;   // slot-space adjoints
     float *hbar = nullptr, *rho = nullptr, *rnbar = nullptr;   // dense per-node fields
     float4 *nbar = nullptr;
@@ -154,6 +156,8 @@ void free_all(Batch &b) {
   Batch::Adj &a = b.adj;
   for (float *p : a.cp) cudaFree(p);
   for (float *p : a.store) cudaFree(p);
+  for (float *p : a.seg_rhoN) cudaFree(p);
+  for (float4 *p : a.seg_nrm) cudaFree(p);
   void *aptrs[] = {a.lam0, a.lam1, a.fbar, a.hbar, a.rho, a.rnbar, a.nbar, a.coef, a.thbar, a.uin};
   for (void *p : aptrs) cudaFree(p);
   a = Batch::Adj{};
@@ -1011,8 +1015,26 @@ int adj_alloc(Batch &b, int64_t nseg, int64_t K) {
   }
   while ((int64_t)a.store.size() < K) {
     float *p = nullptr;
-    if (!grab((void **)&p, sb)) return LBM_ENOMEM;
+    float *r = nullptr;
+    float4 *q = nullptr;
+    if (!grab((void **)&p, sb) || !grab((void **)&r, nodes * sizeof(float)) ||
+        !grab((void **)&q, nodes * sizeof(float4))) {
+      cudaFree(p);
+      cudaFree(r);
+      cudaFree(q);
+      return LBM_ENOMEM;
+    }
+    // interior solids are never written and read as zero by the stencils
+    if (cudaMemset(r, 0, nodes * sizeof(float)) != cudaSuccess ||
+        cudaMemset(q, 0, nodes * sizeof(float4)) != cudaSuccess) {
+      cudaFree(p);
+      cudaFree(r);
+      cudaFree(q);
+      return LBM_ECUDA;
+    }
     a.store.push_back(p);
+    a.seg_rhoN.push_back(r);
+    a.seg_nrm.push_back(q);
   }
   return LBM_OK;
 }
@@ -1053,7 +1075,17 @@ int adjoint_forward(Batch &b, int64_t nsteps, int64_t every, double *objective) 
   return LBM_OK;
 }
 
-// lambda_t from lambda_{t+1} (lam_in) and the state f_t
+// the forward fields of state fin (rho^N, colour at solids, wetted normals, normals
+// at solids) into b.rhoN / b.nrm
+void launch_fields(Batch &b, cudaStream_t st, const float *fin) {
+  launch_density<float>(b, st, fin);
+  if (b.n_bnd > 0) launch_solids(b, st, true);
+  launch_normal(b, st);
+  if (b.n_bnd > 0) launch_solids(b, st, false);
+}
+
+// lambda_t from lambda_{t+1} (lam_in) and the state f_t, whose forward fields are
+// in b.rhoN / b.nrm
 int reverse_step(Batch &b, const float *ft, const float *lam_in, float *lam_out) {
   Batch::Adj &a = b.adj;
   const cudaStream_t st = b.stream;
@@ -1061,11 +1093,6 @@ int reverse_step(Batch &b, const float *ft, const float *lam_in, float *lam_out)
   const Inst &I = b.h[0].d;
   const unsigned g128 = (unsigned)((S.nslots + 127) / 128), g256 = (unsigned)((S.nslots + 255) / 256);
   const unsigned gb = (unsigned)((b.n_bnd + 255) / 256);
-  // forward quantities of step t
-  launch_density<float>(b, st, ft);
-  if (b.n_bnd > 0) launch_solids(b, st, true);
-  launch_normal(b, st);
-  if (b.n_bnd > 0) launch_solids(b, st, false);
   CK(cudaMemsetAsync(a.nbar, 0, (size_t)b.nodes * sizeof(float4), st));
   CK(cudaMemsetAsync(a.rnbar, 0, (size_t)b.nodes * sizeof(float), st));
   k_adj_collide<<<g128, 128, 0, st>>>(S, I, ft, b.gidx, b.link, b.nrm, lam_in, a.fbar, a.nbar, a.hbar, a.rho);
@@ -1098,19 +1125,31 @@ int adjoint_backward(Batch &b, double seed, double *dtheta, double *du_in, float
                                                                        (float)a_out, a.lam0);
   CK(cudaGetLastError());
   float *lam = a.lam0, *lamn = a.lam1;
-  for (int64_t s = a.nseg - 1; s >= 0; --s) {
+  float *const rhoN0 = b.rhoN;
+  float4 *const nrm0 = b.nrm;
+  int rc = LBM_OK;
+  for (int64_t s = a.nseg - 1; s >= 0 && rc == LBM_OK; --s) {
     const int64_t t0 = s * a.K, t1 = std::min(t0 + a.K, a.nsteps);
     CK(cudaMemcpyAsync(a.store[0], a.cp[s], sb, cudaMemcpyDeviceToDevice, b.stream));
-    for (int64_t t = t0 + 1; t < t1; ++t)
-      enqueue_step(b, b.stream, a.store[t - 1 - t0], a.store[t - t0], 0, false, b.acc_scratch);
-    CK(cudaGetLastError());
-    for (int64_t t = t1 - 1; t >= t0; --t) {
-      const int rc = reverse_step(b, a.store[t - t0], lam, lamn);
-      if (rc) return rc;
+    // recompute the segment, keeping every state and its forward fields
+    for (int64_t t = t0; t < t1; ++t) {
+      const int64_t j = t - t0;
+      b.rhoN = a.seg_rhoN[j];
+      b.nrm = a.seg_nrm[j];
+      launch_fields(b, b.stream, a.store[j]);
+      if (t + 1 < t1) launch_main<float>(b, b.stream, a.store[j], a.store[j + 1], b.acc_scratch, 0);
+    }
+    if (cudaGetLastError() != cudaSuccess) rc = LBM_ECUDA;
+    for (int64_t t = t1 - 1; t >= t0 && rc == LBM_OK; --t) {
+      b.rhoN = a.seg_rhoN[t - t0];
+      b.nrm = a.seg_nrm[t - t0];
+      rc = reverse_step(b, a.store[t - t0], lam, lamn);
       std::swap(lam, lamn);
     }
   }
-  // the step kernels left rho^N and the normals of an early step in the dense fields
+  b.rhoN = rhoN0;
+  b.nrm = nrm0;
+  if (rc) return cuda_fail(b, cudaErrorUnknown);
   if (dtheta) {
     CK(cudaMemcpyAsync(dtheta, a.thbar, (size_t)ih.d.L.n * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   }

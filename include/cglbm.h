@@ -144,6 +144,15 @@ int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
  * Either pointer may be NULL.  This is the cheap per-step result read. */
 int lbm_reaction(lbm_ctx *ctx, double *rate, double *consumed);
 
+/* The same two values without synchronising: enqueues on the context's stream
+ * copies of the last step's sum of delta into dst[0] and the cumulative sum into
+ * dst[1] (host memory; page-locked memory keeps the copy asynchronous).  dst must
+ * stay valid until the copies have run, i.e. until the next synchronising call on
+ * the context or a synchronisation of its stream.  Call it before the next
+ * lbm_step (the per-step slot is reused two steps later).  LBM_EINVAL before the
+ * first step. */
+int lbm_reaction_async(lbm_ctx *ctx, double *dst);
+
 /* Equilibrium start from host fields of N floats each (u: 3*N, [3][N], or
  * NULL for rest): f^r = f^eq(rho_r, u), f^p = f^eq(rho_p, u), g = g^eq(conc, u).
  * Resets step, consumed and m^C(0). */

@@ -1305,6 +1305,17 @@ int lbm_reaction(lbm_ctx *c, double *rate, double *consumed) {
   return LBM_OK;
 }
 
+int lbm_reaction_async(lbm_ctx *c, double *dst) {
+  if (!c || !dst) return LBM_EINVAL;
+  Batch &b = c->b;
+  if (b.sticky) return b.sticky;
+  if (b.step < 1) return LBM_EINVAL;
+  cudaSetDevice(b.device);
+  CK(cudaMemcpyAsync(dst, b.acc + 2 + ((b.step - 1) & 1), sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaMemcpyAsync(dst + 1, b.acc, sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  return LBM_OK;
+}
+
 int lbm_init_fields(lbm_ctx *c, const float *rho_r, const float *rho_p, const float *conc, const float *u) {
   return c ? init_fields(c->b, 0, rho_r, rho_p, conc, u) : LBM_EINVAL;
 }

@@ -33,7 +33,7 @@ SYMBOLS = (
     "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static", "lbm_tune",
     "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables", "lbm_batch_get_state",
     "lbm_batch_set_state", "lbm_batch_tune", "lbm_batch_profile", "lbm_batch_profile_read",
-    "lbm_batch_destroy", "lbm_set_wetting", "lbm_set_inlet", "lbm_adjoint_forward", "lbm_adjoint_backward",
+    "lbm_batch_destroy", "lbm_reaction_async", "lbm_set_wetting", "lbm_set_inlet", "lbm_adjoint_forward", "lbm_adjoint_backward",
 )
 STATIC_MAX_NODES = 131072   # LBM_STATIC_MAX_NODES
 
@@ -135,6 +135,7 @@ def load_library(path=LIB_PATH):
         "lbm_batch_profile": (ctypes.c_int, [P, I32]),
         "lbm_batch_profile_read": (ctypes.c_int, [P, P, P, I32]),
         "lbm_batch_destroy": (None, [P]),
+        "lbm_reaction_async": (ctypes.c_int, [P, P]),
         "lbm_set_wetting": (ctypes.c_int, [P, P]),
         "lbm_set_inlet": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double]),
         "lbm_adjoint_forward": (ctypes.c_int, [P, I64, I64, P]),
@@ -191,6 +192,12 @@ def lbm_reaction(ctx):
     r, c = ctypes.c_double(), ctypes.c_double()
     _check(load_library().lbm_reaction(ctx, ctypes.byref(r), ctypes.byref(c)), "lbm_reaction")
     return r.value, c.value
+
+
+def lbm_reaction_async(ctx, dst_ptr):
+    """Enqueue copies of (rate, consumed) into host memory at address ``dst_ptr`` (two doubles,
+    page-locked), valid after the next synchronisation of the context's stream."""
+    _check(load_library().lbm_reaction_async(ctx, dst_ptr), "lbm_reaction_async")
 
 
 def lbm_init_fields(ctx, rho_r, rho_p, conc, u=None):
@@ -352,6 +359,9 @@ class Lattice:
 
     def reaction(self):
         return lbm_reaction(self.ctx)
+
+    def reaction_async(self, dst_ptr):
+        lbm_reaction_async(self.ctx, dst_ptr)
 
     def init_fields(self, rho_r, rho_p, conc, u=None):
         lbm_init_fields(self.ctx, rho_r, rho_p, conc, u)

@@ -60,6 +60,32 @@ def dist_env():
     return world, rank, local
 
 
+def init_distributed(world, backend):
+    """One process per GPU (replicas): the process group serves the barrier and the
+    max-over-ranks of the timing only; no collective touches the lattice data."""
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def max_over_ranks(v, world, device):
+    """The slowest rank's value (timings are taken as the max over ranks)."""
+    if world > 1:
+        import torch
+
+        tt = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        v = float(tt.item())
+    return v
+
+
+def whole_job_mlups(world, nodes, steps, ms):
+    """Lattice-node updates of all ranks (each advances its own replica) per second, in millions."""
+    return world * nodes * steps / (ms * 1e-3) / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -243,9 +269,7 @@ def run_native(args):
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    init_distributed(world, "nccl")
     from paper_2608_15781_b300 import build, lbm
     from paper_2608_15781_b300.configs import WORKLOADS
 
@@ -264,13 +288,6 @@ def run_native(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if world > 1:
-            tt = torch.tensor([v], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            v = float(tt.item())
-        return v
-
     def measure(params, steps, warmup, clocks=None):
         """K timed steps, per-kernel CUDA events on the launching stream; time = max over ranks."""
         L = lbm.Lattice(solid, params, bc_z=wl.bc_z, stream=stream.cuda_stream)
@@ -287,7 +304,7 @@ def run_native(args):
         e1.record(stream)
         barrier()
         clk = clocks.stop() if clocks else None
-        t = max_over_ranks(e0.elapsed_time(e1))
+        t = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         ob = L.observables()
         # per-kernel split: a separate run with CUDA events around every launch (no graphs)
         psteps = steps
@@ -311,7 +328,7 @@ def run_native(args):
     head = dataclasses.replace(wl.params, storage=1 if args.storage == "fp16" else 0)
     t_ms, prof, info, ob, clk = measure(head, args.steps, args.warmup, ClockSampler(gpu_idx))
     Nf = info["n_fluid"]
-    value = world * N * args.steps / (t_ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, N, args.steps, t_ms)
     kname, per_node, alg_bytes, achieved = roofline(head, prof, Nf)
     traf = ncu_traffic_per_fluid_node() if (kname == "main" and head.storage == 0) else None
     psteps = args.steps
@@ -325,7 +342,7 @@ def run_native(args):
         tv, pv, _, obv, _ = measure(other, vsteps, args.warmup)
         kv, pnv, _, achv = roofline(other, pv, Nf)
         variants["fp16_storage" if other.storage == 1 else "fp32_storage"] = {
-            "value": round(world * N * vsteps / (tv * 1e-3) / 1e6, 2), "unit": UNIT, "steps": vsteps,
+            "value": round(whole_job_mlups(world, N, vsteps, tv), 2), "unit": UNIT, "steps": vsteps,
             "ms_per_step": round(tv / vsteps, 5), "dtype": "f16 storage, f32 math" if other.storage else "f32",
             "roofline": {"kernel": f"k_{kv}", "achieved": round(achv, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
@@ -351,12 +368,12 @@ def run_native(args):
         ob2 = L2.observables()                      # synchronises the stream
         L2.close()
         torch.cuda.synchronize()
-        te = max_over_ranks(time.perf_counter() - t0)
+        te = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         rates = ring.numpy().reshape(-1, 2)
         assert abs(rates[-1, 1] - ob2["consumed"]) <= 1e-9 * max(1.0, abs(ob2["consumed"]))
         h2d = N * 1                                  # the mask
         d2h = 16 * args.steps + 4 * N + 8 * 8 * 2    # reaction sums per step, link readback, observables
-        e2e = {"value": round(world * N * args.steps / te / 1e6, 2), "unit": UNIT,
+        e2e = {"value": round(whole_job_mlups(world, N, args.steps, te * 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": round(h2d / args.steps, 2), "d2h_bytes_per_step": round(d2h / args.steps, 2),
                "includes": "lbm_create from the host mask (geometry precompute on the GPU, slot layout on the "
                            "host), per step lbm_step(1) + lbm_reaction_async (D2H of the step's reaction sums "
@@ -420,7 +437,7 @@ def measure_batched(lbm, torch, stream, world, steps, warmup, seq_steps=20):
     B.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_b = e0.elapsed_time(e1)
+    t_b = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     B.profile(steps * 6 + 16)
     B.step(steps)
     prof = B.profile_read()
@@ -444,8 +461,9 @@ def measure_batched(lbm, torch, stream, world, steps, warmup, seq_steps=20):
     peak, _ = measured_peaks()
     alg = nf * bytes_per_fluid_node(params[0])
     achieved = alg / (k_ms / k_n * 1e-3) / 1e9
-    v_b = world * nodes * steps / (t_b * 1e-3) / 1e6
-    v_s = nodes * seq_steps / (t_s * 1e-3) / 1e6
+    t_s = max_over_ranks(t_s, world, "cuda")
+    v_b = whole_job_mlups(world, nodes, steps, t_b)
+    v_s = whole_job_mlups(world, nodes, seq_steps, t_s)
     return {"value": round(v_b, 2), "unit": UNIT, "steps": steps, "ms_per_step": round(t_b / steps, 5),
             "workload": f"64 columns, edges {min(edges)}-{max(edges)}, {nodes} nodes, {nf} fluid",
             "blocks": blocks, "sequential_value": round(v_s, 2), "speedup_vs_sequential": round(v_b / v_s, 3),
@@ -478,7 +496,8 @@ def measure_adjoint(lbm, torch, stream, world, nsteps):
     dth, du, _ = L.adjoint_backward()
     e2.record(stream)
     torch.cuda.synchronize()
-    t_f, t_b = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    t_f = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    t_b = max_over_ranks(e1.elapsed_time(e2), world, "cuda")
     K = int(np.ceil(np.sqrt(nsteps)))
     nstate = (nsteps + K - 1) // K + K + 3
     # reverse sweep per step and fluid node: recompute step (361 B) + adjoint step
@@ -486,7 +505,7 @@ def measure_adjoint(lbm, torch, stream, world, nsteps):
     rev_bytes = nf * (361 + 540) * nsteps
     peak, _ = measured_peaks()
     L.close()
-    return {"value": round(world * N * nsteps / ((t_f + t_b) * 1e-3) / 1e6, 2), "unit": "MLUPS (forward+backward)",
+    return {"value": round(whole_job_mlups(world, N, nsteps, t_f + t_b), 2), "unit": "MLUPS (forward+backward)",
             "workload": f"column96 (96^3, shell 6, porosity 0.5, u_in 0.004, k 2e-3), {nf} fluid, after 200 steps",
             "steps": nsteps, "checkpoint_every": K, "checkpoint_states": nstate,
             "ms_forward": round(t_f, 2), "ms_backward": round(t_b, 2), "objective": J,

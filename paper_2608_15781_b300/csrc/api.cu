@@ -564,48 +564,63 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   std::vector<uint32_t> hnode, hbnd;
   std::vector<uint16_t> hkid, hbkid;
   std::vector<int> hgidx((size_t)gtot, -1);
+  {
+    long long ghost_slots = 0;
+    for (int k = 0; k < n; ++k) ghost_slots += b.h[k].d.L.bc_z == 1 ? 2 * b.h[k].d.L.plane : 0;
+    hnode.reserve((size_t)(nodes + ghost_slots));
+    if (n > 1) hkid.reserve((size_t)(nodes + ghost_slots));
+  }
   long long s = 0;
   for (int k = 0; k < n; ++k) {
     InstHost &ih = b.h[k];
     const Lattice &L = ih.d.L;
     const uint32_t *lk = hlink.data() + ih.d.node_off;
-    int *gi = hgidx.data() + ih.d.gidx_off;
+    int *gi = hgidx.data() + ih.d.gidx_off + L.plane;   // gi[node index], planes -1 and nz outside
     ih.d.slot_off = (int)s;
-    for (long long i = 0; i < L.n; ++i) {
-      const uint32_t x = (uint32_t)(i % L.nx), y = (uint32_t)((i / L.nx) % L.ny), z = (uint32_t)(i / L.plane);
-      const uint32_t pk = x | (y << 10) | (z << 20);
-      if (lk[i] & BIT_SOLID_BND) {
-        hbnd.push_back(pk);
-        hbkid.push_back((uint16_t)k);
-        ih.n_bnd++;
-      }
-      if (lk[i] & BIT_WALL) ih.n_wall++;
-      if (!(lk[i] & BIT_SOLID)) {
-        gi[i + L.plane] = (int)s;
-        ih.slot_node.push_back((uint32_t)i);
-        hnode.push_back(pk);
-        hkid.push_back((uint16_t)k);
-        ++s;
-      }
-    }
+    ih.slot_node.reserve((size_t)L.n);
+    long long i = 0;
+    for (uint32_t z = 0; z < (uint32_t)L.nz; ++z)
+      for (uint32_t y = 0; y < (uint32_t)L.ny; ++y)
+        for (uint32_t x = 0; x < (uint32_t)L.nx; ++x, ++i) {
+          const uint32_t w = lk[i];
+          const uint32_t pk = x | (y << 10) | (z << 20);
+          if (w & BIT_SOLID) {
+            if (w & BIT_SOLID_BND) {
+              hbnd.push_back(pk);
+              if (n > 1) hbkid.push_back((uint16_t)k);
+              ih.n_bnd++;
+            }
+            continue;
+          }
+          if (w & BIT_WALL) ih.n_wall++;
+          gi[i] = (int)s;
+          ih.slot_node.push_back((uint32_t)i);
+          hnode.push_back(pk);
+          if (n > 1) hkid.push_back((uint16_t)k);
+          ++s;
+        }
     ih.d.nf = (int)(s - ih.d.slot_off);
     ih.n_fluid = ih.d.nf;
     if (ih.n_fluid == 0) return LBM_EINVAL;
     ih.d.ghost = (int)s;
     if (L.bc_z == 1) {
       for (long long q = 0; q < L.plane; ++q) {
-        gi[q] = (int)(s + q);                                   // inlet plane
-        gi[(L.nz + 1) * L.plane + q] = (int)(s + L.plane + q);  // outlet plane
+        gi[q - L.plane] = (int)(s + q);                         // inlet plane z = -1
+        gi[L.nz * L.plane + q] = (int)(s + L.plane + q);        // outlet plane z = nz
       }
       for (long long q = 0; q < 2 * L.plane; ++q) {
         hnode.push_back(kNoNode);
-        hkid.push_back((uint16_t)k);
+        if (n > 1) hkid.push_back((uint16_t)k);
       }
       s += 2 * L.plane;
     }
     if (s > (1ll << 31) - 1) return LBM_EINVAL;
   }
   b.nslots = (int)s;
+  // every slot-map entry is a slot of the space or -1 (solid): the kernels index
+  // population arrays with these values
+  for (int v : hgidx)
+    if (v < -1 || v >= b.nslots) return LBM_EINVAL;
   b.ns = (int)((s + 63) / 64 * 64);
   if ((long long)NPOP * b.ns >= (1ll << 32)) return LBM_EINVAL;   // 32-bit population offsets
   b.n_bnd = (int)hbnd.size();

@@ -189,7 +189,7 @@ __device__ __forceinline__ const Inst &inst_of(const Slots &S, const Inst &singl
 }
 
 template <typename T, int BLOCK, bool BATCH>
-__global__ void __launch_bounds__(BLOCK) k_density_c(Slots S, const __grid_constant__ Inst single,
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, const __grid_constant__ Inst single,
                                                      const T *__restrict__ f, const int *__restrict__ gidx,
                                                      float *__restrict__ rhoN) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;

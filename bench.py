@@ -351,6 +351,10 @@ def run_native(args):
     if not args.no_variants:
         variants["batched"] = measure_batched(lbm, torch, stream, world, max(args.steps // 10, 20), args.warmup)
         variants["adjoint"] = measure_adjoint(lbm, torch, stream, world, 3000 if args.steps >= 1000 else 300)
+        variants["precision_periodic256"] = measure_precision(lbm, torch, stream, world,
+                                                              5000 if args.steps >= 1000 else 200)
+        variants["column_series"] = measure_series(lbm, torch, stream, wl, head,
+                                                   20000 if args.steps >= 1000 else 400, 10)
 
     # end to end through the C ABI with host buffers: create from the host mask,
     # K x (step + copy of the step's reaction sums into pinned host memory), observables, destroy
@@ -469,6 +473,86 @@ def measure_batched(lbm, torch, stream, world, steps, warmup, seq_steps=20):
             "blocks": blocks, "sequential_value": round(v_s, 2), "speedup_vs_sequential": round(v_b / v_s, 3),
             "roofline": {"kernel": "k_main", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4)}}
+
+
+_C19 = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 0], [1, -1, 0],
+                 [1, 0, 1], [1, 0, -1], [-1, 1, 0], [-1, -1, 0], [-1, 0, 1], [-1, 0, -1], [0, 1, 1], [0, 1, -1],
+                 [0, -1, 1], [0, -1, -1], [0, 0, 0]], dtype=np.float64)
+
+
+def velocity_difference(fa, fb, solid, chunk=16):
+    """(max |u_a - u_b|, max |u_b|) over the fluid nodes of two (45, nz, ny, nx) states, in z chunks."""
+    fl_all = ~solid.astype(bool)
+    dmax = umax = 0.0
+    for z0 in range(0, solid.shape[0], chunk):
+        sl = slice(z0, z0 + chunk)
+        fl = fl_all[sl]
+        us = []
+        for f in (fa, fb):
+            m = f[0:19, sl].astype(np.float64) + f[19:38, sl]
+            rho = np.where(fl, m.sum(0), 1.0)
+            us.append(np.einsum("ia,i...->a...", _C19, m) / rho)
+        dmax = max(dmax, float(np.abs(us[0] - us[1])[:, fl].max()))
+        umax = max(umax, float(np.abs(us[1])[:, fl].max()))
+    return dmax, umax
+
+
+def measure_precision(lbm, torch, stream, world, nsteps):
+    """256^3 periodic workload: FP32 and FP16 population storage from the same start,
+    MLUPS of each and the FP16 - FP32 differences of conversion, gas saturation and u."""
+    from paper_2608_15781_b300.configs import WORKLOADS
+
+    wl = WORKLOADS["periodic256"]
+    solid = wl.mask()
+    out = {"workload": f"periodic256 (256^3, shell 12, porosity 0.5, seed 3), {nsteps} steps from rest"}
+    res = {}
+    # the third run: FP32 from a start perturbed by 1e-6 (the trajectories' own spread)
+    rng = np.random.default_rng(0)
+    perturbed = (1.0 + 1e-6 * rng.standard_normal(solid.shape)).astype(np.float32)
+    for name, storage, rho_r in (("fp32", 0, np.ones(solid.shape, np.float32)),
+                                 ("fp16", 1, np.ones(solid.shape, np.float32)),
+                                 ("fp32_perturbed", 0, perturbed)):
+        L = lbm.Lattice(solid, dataclasses.replace(wl.params, storage=storage), bc_z=0, stream=stream.cuda_stream)
+        L.step(3)
+        L.init_fields(rho_r, np.zeros(solid.shape, np.float32), np.full(solid.shape, wl.params.c_init, np.float32))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.step(nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+        ob = L.observables()
+        res[name] = (ob, L.get_state())
+        if name != "fp32_perturbed":
+            out[f"{name}_mlups"] = round(whole_job_mlups(world, solid.size, nsteps, ms), 2)
+        L.close()
+    (o32, f32), (o16, f16), (op_, fp_) = res["fp32"], res["fp16"], res["fp32_perturbed"]
+    out["conversion_fp32"] = o32["conversion"]
+    out["gas_saturation_fp32"] = o32["gas_saturation"]
+    out["fp16_vs_fp32"] = {"abs_diff_conversion": abs(o16["conversion"] - o32["conversion"]),
+                           "abs_diff_gas_saturation": abs(o16["gas_saturation"] - o32["gas_saturation"])}
+    out["fp16_vs_fp32"]["max_abs_diff_u"], out["max_abs_u_fp32"] = velocity_difference(f16, f32, solid)
+    out["fp32_spread_1e-6_start"] = {"abs_diff_conversion": abs(op_["conversion"] - o32["conversion"]),
+                                     "abs_diff_gas_saturation": abs(op_["gas_saturation"] - o32["gas_saturation"])}
+    out["fp32_spread_1e-6_start"]["max_abs_diff_u"], _ = velocity_difference(fp_, f32, solid)
+    out["n_bad"] = int(o16["n_bad"] + o32["n_bad"] + op_["n_bad"])
+    return out
+
+
+def measure_series(lbm, torch, stream, wl, params, nsteps, samples):
+    """The headline column run for nsteps steps: conversion and gas saturation every nsteps/samples steps."""
+    solid = wl.mask()
+    L = lbm.Lattice(solid, params, bc_z=wl.bc_z, stream=stream.cuda_stream)
+    every = max(nsteps // samples, 1)
+    series = []
+    for k in range(samples):
+        L.step(every)
+        ob = L.observables()
+        series.append([(k + 1) * every, round(ob["conversion"], 6), round(ob["gas_saturation"], 6)])
+    L.close()
+    return {"workload": wl.name, "steps": every * samples, "series_step_conversion_saturation": series,
+            "n_bad": int(ob["n_bad"])}
 
 
 def measure_adjoint(lbm, torch, stream, world, nsteps):

@@ -335,27 +335,6 @@ def run_native(args):
     # the timed region replays one graph per step holding the same launches as a profiled step
     launches = int(round(sum(n for _, n in prof.values()) / psteps * args.steps))
 
-    variants = {}
-    if not args.no_variants:
-        other = dataclasses.replace(head, storage=1 - head.storage)
-        vsteps = max(args.steps // 2, 1)
-        tv, pv, _, obv, _ = measure(other, vsteps, args.warmup)
-        kv, pnv, _, achv = roofline(other, pv, Nf)
-        variants["fp16_storage" if other.storage == 1 else "fp32_storage"] = {
-            "value": round(whole_job_mlups(world, N, vsteps, tv), 2), "unit": UNIT, "steps": vsteps,
-            "ms_per_step": round(tv / vsteps, 5), "dtype": "f16 storage, f32 math" if other.storage else "f32",
-            "roofline": {"kernel": f"k_{kv}", "achieved": round(achv, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
-            "conversion": obv["conversion"], "gas_saturation": obv["gas_saturation"]}
-
-    if not args.no_variants:
-        variants["batched"] = measure_batched(lbm, torch, stream, world, max(args.steps // 10, 20), args.warmup)
-        variants["adjoint"] = measure_adjoint(lbm, torch, stream, world, 3000 if args.steps >= 1000 else 300)
-        variants["precision_periodic256"] = measure_precision(lbm, torch, stream, world,
-                                                              5000 if args.steps >= 1000 else 200)
-        variants["column_series"] = measure_series(lbm, torch, stream, wl, head,
-                                                   20000 if args.steps >= 1000 else 400, 10)
-
     # end to end through the C ABI with host buffers: create from the host mask,
     # K x (step + copy of the step's reaction sums into pinned host memory), observables, destroy
     e2e = None
@@ -382,6 +361,27 @@ def run_native(args):
                "includes": "lbm_create from the host mask (geometry precompute on the GPU, slot layout on the "
                            "host), per step lbm_step(1) + lbm_reaction_async (D2H of the step's reaction sums "
                            "into pinned memory), lbm_observables (synchronises), lbm_destroy"}
+
+    variants = {}
+    if not args.no_variants:
+        other = dataclasses.replace(head, storage=1 - head.storage)
+        vsteps = max(args.steps // 2, 1)
+        tv, pv, _, obv, _ = measure(other, vsteps, args.warmup)
+        kv, pnv, _, achv = roofline(other, pv, Nf)
+        variants["fp16_storage" if other.storage == 1 else "fp32_storage"] = {
+            "value": round(whole_job_mlups(world, N, vsteps, tv), 2), "unit": UNIT, "steps": vsteps,
+            "ms_per_step": round(tv / vsteps, 5), "dtype": "f16 storage, f32 math" if other.storage else "f32",
+            "roofline": {"kernel": f"k_{kv}", "achieved": round(achv, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
+            "conversion": obv["conversion"], "gas_saturation": obv["gas_saturation"]}
+
+    if not args.no_variants:
+        variants["batched"] = measure_batched(lbm, torch, stream, world, max(args.steps // 10, 20), args.warmup)
+        variants["adjoint"] = measure_adjoint(lbm, torch, stream, world, 3000 if args.steps >= 1000 else 300)
+        variants["precision_periodic256"] = measure_precision(lbm, torch, stream, world,
+                                                              5000 if args.steps >= 1000 else 200)
+        variants["column_series"] = measure_series(lbm, torch, stream, wl, head,
+                                                   20000 if args.steps >= 1000 else 400, 10)
 
     if rank != 0:
         return 0

@@ -179,11 +179,17 @@ int lbm_set_debug(lbm_ctx *ctx, int32_t enable);
 int lbm_profile(lbm_ctx *ctx, int32_t enable);
 int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
-/* Pick the launch shapes of the main, colour-function and normal kernels by
- * timing each candidate (main: 64/128/256 threads; others 128/256/512) on the
- * current state; blocks[3] (may be NULL) receives the choice.  The state is not
- * advanced.  Without a call the defaults (128, 256, 256) are used. */
+/* Launch shapes of the step (not part of the paper): lbm_tune times each
+ * candidate on the current state (main kernel 64/128/256 threads; colour-function
+ * and normal kernels 128/256/512) and keeps the fastest; blocks[3] (may be NULL)
+ * receives the choice (main, density, normal).  The state is not advanced.
+ * Without a call the defaults (128, 256, 256) are used. */
 int lbm_tune(lbm_ctx *ctx, int32_t *blocks);
+
+/* Set the launch shapes directly (blocks[3] as filled by lbm_tune, e.g. a tuning
+ * saved earlier).  LBM_EINVAL for a value outside the candidates.  The next step
+ * rebuilds the step's CUDA graphs. */
+int lbm_set_launch(lbm_ctx *ctx, const int32_t *blocks);
 
 /* Static counts: fluid nodes, wall nodes, solid nodes next to the fluid,
  * device bytes held.  Any pointer may be NULL. */
@@ -256,6 +262,7 @@ int lbm_batch_observables(lbm_batch *batch, lbm_obs *out, int32_t count);
 int lbm_batch_get_state(lbm_batch *batch, int32_t k, float *host_dst, size_t bytes);
 int lbm_batch_set_state(lbm_batch *batch, int32_t k, const float *host_src, size_t bytes);
 int lbm_batch_tune(lbm_batch *batch, int32_t *blocks);
+int lbm_batch_set_launch(lbm_batch *batch, const int32_t *blocks);
 int lbm_batch_profile(lbm_batch *batch, int32_t max_launches);
 int lbm_batch_profile_read(lbm_batch *batch, double *ms, int64_t *launches, int32_t n);
 void lbm_batch_destroy(lbm_batch *batch);

@@ -296,17 +296,18 @@ void launch_main(const Batch &b, cudaStream_t st, const void *fin, void *fout, d
 
 void launch_solids(const Batch &b, cudaStream_t st, bool colour) {
   const Inst &I = b.h[0].d;
-  const unsigned g = (unsigned)((b.n_bnd + 255) / 256);
+  const unsigned g = (unsigned)((b.n_bnd + 127) / 128);
   if (colour) {
     if (b.n > 1)
-      k_color_solid_c<true><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+      k_color_solid_c<true><<<g, 128, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
     else
-      k_color_solid_c<false><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+      k_color_solid_c<false><<<g, 128, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
   } else {
+    const unsigned g256 = (unsigned)((b.n_bnd + 255) / 256);
     if (b.n > 1)
-      k_normal_solid_c<true><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+      k_normal_solid_c<true><<<g256, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
     else
-      k_normal_solid_c<false><<<g, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+      k_normal_solid_c<false><<<g256, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
   }
 }
 
@@ -854,6 +855,18 @@ int tune(Batch &b, int32_t *chosen) {
   return LBM_OK;
 }
 
+int set_launch(Batch &b, const int32_t *blocks) {
+  if (!blocks) return LBM_EINVAL;
+  const auto one_of = [](int v, int a, int c, int d) { return v == a || v == c || v == d; };
+  if (!one_of(blocks[0], 64, 128, 256) || !one_of(blocks[1], 128, 256, 512) || !one_of(blocks[2], 128, 256, 512))
+    return LBM_EINVAL;
+  b.main_block = blocks[0];
+  b.dens_block = blocks[1];
+  b.norm_block = blocks[2];
+  drop_graphs(b);
+  return LBM_OK;
+}
+
 int get_field(Batch &b, int k, int32_t which, float *dst, size_t bytes) {
   if (!dst || k < 0 || k >= b.n) return LBM_EINVAL;
   if (b.sticky) return b.sticky;
@@ -1355,6 +1368,8 @@ int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches, int32_t n) {
 
 int lbm_tune(lbm_ctx *c, int32_t *blocks) { return c ? tune(c->b, blocks) : LBM_EINVAL; }
 
+int lbm_set_launch(lbm_ctx *c, const int32_t *blocks) { return c ? set_launch(c->b, blocks) : LBM_EINVAL; }
+
 int lbm_info(lbm_ctx *c, int64_t *n_fluid, int64_t *n_wall, int64_t *n_solid_bnd, int64_t *device_bytes) {
   if (!c) return LBM_EINVAL;
   if (n_fluid) *n_fluid = c->b.h[0].n_fluid;
@@ -1416,6 +1431,10 @@ int lbm_batch_set_state(lbm_batch *bt, int32_t k, const float *src, size_t bytes
 }
 
 int lbm_batch_tune(lbm_batch *bt, int32_t *blocks) { return bt ? tune(bt->b, blocks) : LBM_EINVAL; }
+
+int lbm_batch_set_launch(lbm_batch *bt, const int32_t *blocks) {
+  return bt ? set_launch(bt->b, blocks) : LBM_EINVAL;
+}
 
 int lbm_batch_profile(lbm_batch *bt, int32_t max_launches) { return bt ? profile(bt->b, max_launches) : LBM_EINVAL; }
 

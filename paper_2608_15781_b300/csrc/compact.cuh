@@ -262,9 +262,14 @@ __global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const __grid_consta
 
 // a3 / solid normals over the list of solid nodes next to the fluid (packed
 // coordinates, instance array kid or null); a solid node's link word marks in
-// bit i whether x + c_i is fluid
+// bit i whether x + c_i is fluid.  The colour average loads all 18 neighbour
+// values unconditionally (every neighbour index is inside the lattice) and drops
+// the solid ones by a select, so the loads are in flight together instead of one
+// branch at a time (17 -> 15 us on the 128x128x256 column); for the float4
+// normals the same form doubles the loaded bytes and is slower, so they keep the
+// conditional loads.
 template <bool BATCH>
-__global__ void k_color_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
+__global__ void __launch_bounds__(128) k_color_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
                                 const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
                                 const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,13 +281,15 @@ __global__ void k_color_solid_c(const Inst *__restrict__ inst, const __grid_cons
   St.init(I.L, x, y, z);
   float *rn = rhoN + I.node_off;
   const uint32_t lk = link[I.node_off + St.own];
+  float v[Q - 1];
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) v[i] = rn[St.nb(CX[i], CY[i], CZ[i])];
   float num = 0.f, den = 0.f;
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) {
-    if ((lk >> i) & 1u) {
-      num += W[i] * rn[St.nb(CX[i], CY[i], CZ[i])];
-      den += W[i];
-    }
+    const bool fl = (lk >> i) & 1u;
+    num += fl ? W[i] * v[i] : 0.f;
+    den += fl ? W[i] : 0.f;
   }
   rn[St.own] = den > 0.f ? num / den : 0.f;
 }

@@ -30,9 +30,9 @@ KERNEL_NAMES = ("density", "color_solid", "normal", "normal_solid", "main", "obs
 SYMBOLS = (
     "lbm_create", "lbm_step", "lbm_observables", "lbm_reaction", "lbm_init_fields", "lbm_get_state",
     "lbm_set_state", "lbm_get_field", "lbm_set_debug", "lbm_profile", "lbm_profile_read",
-    "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static", "lbm_tune",
+    "lbm_info", "lbm_destroy", "lbm_strerror", "lbm_step_static", "lbm_tune", "lbm_set_launch",
     "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables", "lbm_batch_get_state",
-    "lbm_batch_set_state", "lbm_batch_tune", "lbm_batch_profile", "lbm_batch_profile_read",
+    "lbm_batch_set_state", "lbm_batch_tune", "lbm_batch_set_launch", "lbm_batch_profile", "lbm_batch_profile_read",
     "lbm_batch_destroy", "lbm_reaction_async", "lbm_set_wetting", "lbm_set_inlet", "lbm_adjoint_forward", "lbm_adjoint_backward",
 )
 STATIC_MAX_NODES = 131072   # LBM_STATIC_MAX_NODES
@@ -125,6 +125,7 @@ def load_library(path=LIB_PATH):
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_step_static": (ctypes.c_int, [I32, I32, I32, P, P, P, P, P, ctypes.POINTER(_Params)]),
         "lbm_tune": (ctypes.c_int, [P, P]),
+        "lbm_set_launch": (ctypes.c_int, [P, P]),
         "lbm_batch_create": (ctypes.c_int, [I32, ctypes.POINTER(_Geometry), ctypes.POINTER(_Params), P,
                                             ctypes.POINTER(P)]),
         "lbm_batch_step": (ctypes.c_int, [P, I64]),
@@ -132,6 +133,7 @@ def load_library(path=LIB_PATH):
         "lbm_batch_get_state": (ctypes.c_int, [P, I32, P, SZ]),
         "lbm_batch_set_state": (ctypes.c_int, [P, I32, P, SZ]),
         "lbm_batch_tune": (ctypes.c_int, [P, P]),
+        "lbm_batch_set_launch": (ctypes.c_int, [P, P]),
         "lbm_batch_profile": (ctypes.c_int, [P, I32]),
         "lbm_batch_profile_read": (ctypes.c_int, [P, P, P, I32]),
         "lbm_batch_destroy": (None, [P]),
@@ -247,11 +249,24 @@ def lbm_info(ctx):
     return dict(n_fluid=v[0].value, n_wall=v[1].value, n_solid_bnd=v[2].value, device_bytes=v[3].value)
 
 
+def _launch_dict(blocks):
+    return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]))
+
+
+def _launch_array(launch):
+    return np.array([launch["main"], launch["density"], launch["normal"]], dtype=np.int32)
+
+
 def lbm_tune(ctx):
-    """Time the candidate launch shapes on the current state and keep the fastest; returns them."""
+    """Time the candidate launch configurations on the current state and keep the fastest; returns it."""
     blocks = np.zeros(3, dtype=np.int32)
     _check(load_library().lbm_tune(ctx, _ptr(blocks)), "lbm_tune")
-    return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]))
+    return _launch_dict(blocks)
+
+
+def lbm_set_launch(ctx, launch):
+    """Set the launch configuration (a dict as returned by lbm_tune)."""
+    _check(load_library().lbm_set_launch(ctx, _ptr(_launch_array(launch))), "lbm_set_launch")
 
 
 def lbm_set_wetting(ctx, theta):
@@ -390,6 +405,9 @@ class Lattice:
     def tune(self):
         return lbm_tune(self.ctx)
 
+    def set_launch(self, launch):
+        lbm_set_launch(self.ctx, launch)
+
     def set_wetting(self, theta):
         lbm_set_wetting(self.ctx, theta)
 
@@ -451,7 +469,10 @@ class Batch:
     def tune(self):
         blocks = np.zeros(3, dtype=np.int32)
         _check(load_library().lbm_batch_tune(self.handle, _ptr(blocks)), "lbm_batch_tune")
-        return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]))
+        return _launch_dict(blocks)
+
+    def set_launch(self, launch):
+        _check(load_library().lbm_batch_set_launch(self.handle, _ptr(_launch_array(launch))), "lbm_batch_set_launch")
 
     def profile(self, max_launches):
         _check(load_library().lbm_batch_profile(self.handle, int(max_launches)), "lbm_batch_profile")

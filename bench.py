@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",
+    ap.add_argument("--storage", choices=("fp32", "fp16", "fx16"), default="fp32",
                     help="population storage of the headline run (the other is reported under variants)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="T",
@@ -182,13 +182,13 @@ def bytes_per_fluid_node(params):
     """Algorithmic bytes of one fluid-node update: populations read + written, plus 1 B of flags.
 
     FP32 storage: 361 B with the reactant populations (45 values each way), 305 B
-    in the paper's reaction mode (38); FP16 storage: 181 B / 153 B.  Solid nodes
+    in the paper's reaction mode (38); 2-byte storage (FP16 or 16-bit fixed point): 181 B / 153 B.  Solid nodes
     carry no populations (the library
     stores the fluid nodes only), so a launch's algorithmic traffic is this
     figure times the number of fluid nodes.
     """
     npop = 45 if params.reaction_mode == 0 else 38
-    width = 2 if params.storage == 1 else 4
+    width = 2 if params.storage in (1, 2) else 4
     return 2 * width * npop + 1
 
 
@@ -325,7 +325,7 @@ def run_native(args):
     peak, peak_kind = measured_peaks()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
-    head = dataclasses.replace(wl.params, storage=1 if args.storage == "fp16" else 0)
+    head = dataclasses.replace(wl.params, storage={"fp32": 0, "fp16": 1, "fx16": 2}[args.storage])
     t_ms, prof, info, ob, clk = measure(head, args.steps, args.warmup, ClockSampler(gpu_idx))
     Nf = info["n_fluid"]
     value = whole_job_mlups(world, N, args.steps, t_ms)
@@ -364,16 +364,21 @@ def run_native(args):
 
     variants = {}
     if not args.no_variants:
-        other = dataclasses.replace(head, storage=1 - head.storage)
         vsteps = max(args.steps // 2, 1)
-        tv, pv, _, obv, _ = measure(other, vsteps, args.warmup)
-        kv, pnv, _, achv = roofline(other, pv, Nf)
-        variants["fp16_storage" if other.storage == 1 else "fp32_storage"] = {
-            "value": round(whole_job_mlups(world, N, vsteps, tv), 2), "unit": UNIT, "steps": vsteps,
-            "ms_per_step": round(tv / vsteps, 5), "dtype": "f16 storage, f32 math" if other.storage else "f32",
-            "roofline": {"kernel": f"k_{kv}", "achieved": round(achv, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
-            "conversion": obv["conversion"], "gas_saturation": obv["gas_saturation"]}
+        names = {0: ("fp32_storage", "f32"), 1: ("fp16_storage", "f16 storage, f32 math"),
+                 2: ("fx16_storage", "16-bit fixed-point storage, f32 math")}
+        for st in (0, 1, 2):
+            if st == head.storage:
+                continue
+            other = dataclasses.replace(head, storage=st)
+            tv, pv, _, obv, _ = measure(other, vsteps, args.warmup)
+            kv, pnv, _, achv = roofline(other, pv, Nf)
+            variants[names[st][0]] = {
+                "value": round(whole_job_mlups(world, N, vsteps, tv), 2), "unit": UNIT, "steps": vsteps,
+                "ms_per_step": round(tv / vsteps, 5), "dtype": names[st][1],
+                "roofline": {"kernel": f"k_{kv}", "achieved": round(achv, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achv / peak, 4), "bytes_model": f"{pnv} B per fluid-node update"},
+                "conversion": obv["conversion"], "gas_saturation": obv["gas_saturation"]}
 
     if not args.no_variants:
         variants["batched"] = measure_batched(lbm, torch, stream, world, max(args.steps // 10, 20), args.warmup)
@@ -390,12 +395,13 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16" if head.storage else "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": ["f32", "f16 storage, f32 math", "16-bit fixed-point storage, f32 math"][head.storage],
+        "data": "synthetic",
         "config": {"workload": wl.name, "lattice_xyz": [wl.shape[2], wl.shape[1], wl.shape[0]],
                    "mask": f"GRF shell |k|={wl.shell_k0}+-1, porosity {wl.porosity}, seed {wl.seed}",
                    "fluid_nodes": Nf, "porosity": round(Nf / N, 4),
                    "boundaries": "inlet/outlet in z" if wl.bc_z else "periodic",
-                   "storage": "fp16 deviations" if head.storage else "fp32",
+                   "storage": ["fp32", "fp16 deviations", "16-bit fixed point of f/w"][head.storage],
                    "fluid_mlups": round(world * Nf * args.steps / (t_ms * 1e-3) / 1e6, 2),
                    "l2": "state (2 x 45 x fluid nodes x 4 B) far above the 126 MB L2; no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
@@ -498,20 +504,23 @@ def velocity_difference(fa, fb, solid, chunk=16):
 
 
 def measure_precision(lbm, torch, stream, world, nsteps):
-    """256^3 periodic workload: FP32 and FP16 population storage from the same start,
-    MLUPS of each and the FP16 - FP32 differences of conversion, gas saturation and u."""
+    """256^3 periodic workload: FP32, FP16 and 16-bit fixed-point population storage from
+    the same start, MLUPS of each and the differences of conversion, gas saturation and u
+    against FP32, next to the spread of two FP32 runs from starts 1e-6 apart."""
     from paper_2608_15781_b300.configs import WORKLOADS
 
     wl = WORKLOADS["periodic256"]
     solid = wl.mask()
     out = {"workload": f"periodic256 (256^3, shell 12, porosity 0.5, seed 3), {nsteps} steps from rest"}
-    res = {}
-    # the third run: FP32 from a start perturbed by 1e-6 (the trajectories' own spread)
+    # the last run: FP32 from a start perturbed by 1e-6 (the trajectories' own spread)
     rng = np.random.default_rng(0)
     perturbed = (1.0 + 1e-6 * rng.standard_normal(solid.shape)).astype(np.float32)
+    ref = None
+    n_bad = 0
     for name, storage, rho_r in (("fp32", 0, np.ones(solid.shape, np.float32)),
                                  ("fp16", 1, np.ones(solid.shape, np.float32)),
-                                 ("fp32_perturbed", 0, perturbed)):
+                                 ("fx16", 2, np.ones(solid.shape, np.float32)),
+                                 ("fp32_spread_1e-6_start", 0, perturbed)):
         L = lbm.Lattice(solid, dataclasses.replace(wl.params, storage=storage), bc_z=0, stream=stream.cuda_stream)
         L.step(3)
         L.init_fields(rho_r, np.zeros(solid.shape, np.float32), np.full(solid.shape, wl.params.c_init, np.float32))
@@ -523,20 +532,25 @@ def measure_precision(lbm, torch, stream, world, nsteps):
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         ob = L.observables()
-        res[name] = (ob, L.get_state())
-        if name != "fp32_perturbed":
-            out[f"{name}_mlups"] = round(whole_job_mlups(world, solid.size, nsteps, ms), 2)
+        f = L.get_state()
         L.close()
-    (o32, f32), (o16, f16), (op_, fp_) = res["fp32"], res["fp16"], res["fp32_perturbed"]
-    out["conversion_fp32"] = o32["conversion"]
-    out["gas_saturation_fp32"] = o32["gas_saturation"]
-    out["fp16_vs_fp32"] = {"abs_diff_conversion": abs(o16["conversion"] - o32["conversion"]),
-                           "abs_diff_gas_saturation": abs(o16["gas_saturation"] - o32["gas_saturation"])}
-    out["fp16_vs_fp32"]["max_abs_diff_u"], out["max_abs_u_fp32"] = velocity_difference(f16, f32, solid)
-    out["fp32_spread_1e-6_start"] = {"abs_diff_conversion": abs(op_["conversion"] - o32["conversion"]),
-                                     "abs_diff_gas_saturation": abs(op_["gas_saturation"] - o32["gas_saturation"])}
-    out["fp32_spread_1e-6_start"]["max_abs_diff_u"], _ = velocity_difference(fp_, f32, solid)
-    out["n_bad"] = int(o16["n_bad"] + o32["n_bad"] + op_["n_bad"])
+        n_bad += int(ob["n_bad"])
+        if ref is None:
+            ref = (ob, f)
+            out["fp32_mlups"] = round(whole_job_mlups(world, solid.size, nsteps, ms), 2)
+            out["conversion_fp32"] = ob["conversion"]
+            out["gas_saturation_fp32"] = ob["gas_saturation"]
+            continue
+        key = name if name.startswith("fp32") else f"{name}_vs_fp32"
+        if not name.startswith("fp32"):
+            out[f"{name}_mlups"] = round(whole_job_mlups(world, solid.size, nsteps, ms), 2)
+        d = {"abs_diff_conversion": abs(ob["conversion"] - ref[0]["conversion"]),
+             "abs_diff_gas_saturation": abs(ob["gas_saturation"] - ref[0]["gas_saturation"])}
+        d["max_abs_diff_u"], umax = velocity_difference(f, ref[1], solid)
+        out.setdefault("max_abs_u_fp32", umax)
+        out[key] = d
+        del f
+    out["n_bad"] = n_bad
     return out
 
 

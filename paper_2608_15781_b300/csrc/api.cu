@@ -35,7 +35,8 @@ struct InstHost {
 struct Batch {
   int device = 0;
   cudaStream_t stream = nullptr;
-  bool half = false;                  // FP16 deviation storage
+  bool half = false;                  // 2-byte population storage (storage 1 or 2)
+  int storage = 0;                    // 0 FP32, 1 FP16 deviations, 2 16-bit fixed point
   int n = 0;
   std::vector<InstHost> h;
   // slot space
@@ -169,7 +170,9 @@ int check_params(const lbm_params *p) {
   if (!(p->diffusivity > 0.0) || !std::isfinite(p->diffusivity)) return LBM_EINVAL;
   if (!(p->beta >= 0.0) || !std::isfinite(p->sigma) || !std::isfinite(p->theta_deg)) return LBM_EINVAL;
   if (p->reaction_mode != 0 && p->reaction_mode != 1) return LBM_EINVAL;
-  if (p->storage != 0 && p->storage != 1) return LBM_EINVAL;
+  if (p->storage < 0 || p->storage > 2) return LBM_EINVAL;
+  // 16-bit fixed point covers g / w = C (1 + 4 c.u) up to 1.75
+  if (p->storage == 2 && (!(std::fabs(p->c_init) <= 1.25) || !(std::fabs(p->c_in) <= 1.25))) return LBM_EINVAL;
   if (!(p->k_rate >= 0.0) || !(p->xi >= 0.0) || !(p->rho_out > 0.0)) return LBM_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->accel[a])) return LBM_EINVAL;
@@ -219,7 +222,9 @@ Lattice make_lattice(const lbm_geometry &g) {
 // run f((T *)nullptr) with T the batch's population storage type
 template <class F>
 void with_storage(const Batch &b, F &&f) {
-  if (b.half)
+  if (b.storage == 2)
+    f((uint16_t *)nullptr);
+  else if (b.storage == 1)
     f((__half *)nullptr);
   else
     f((float *)nullptr);
@@ -489,7 +494,8 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   }
   cudaGetDevice(&b.device);
   b.stream = (cudaStream_t)stream;
-  b.half = params[0].storage == 1;
+  b.storage = params[0].storage;
+  b.half = b.storage != 0;
   b.n = n;
   b.h.resize(n);
   // per-instance node / gidx offsets and static geometry
@@ -1456,7 +1462,7 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || ny > 4 * 65535) return LBM_EINVAL;
   const long long n = (long long)nx * ny * nz;
   if (n > (long long)kStaticNodes) return LBM_EINVAL;
-  if (check_params(params) != LBM_OK) return LBM_EINVAL;
+  if (check_params(params) != LBM_OK || params->storage != 0) return LBM_EINVAL;   // FP32 populations only
   const size_t pop_bytes = (size_t)NPOP * n * sizeof(float);
   const char *a = (const char *)f_in, *b = (const char *)f_out;
   if (a < b + pop_bytes && b < a + pop_bytes) return LBM_EINVAL;   // overlap

@@ -19,9 +19,10 @@
 // at the instance's node offset; gidx maps each stored lattice position
 // (plane z + 1 in [0, nz + 1]) to a global slot, or -1 for a solid node.
 //
-// Storage type T: float (FP32) or __half (FP16 deviations from fixed reference
+// Storage type T: float (FP32), __half (FP16 deviations from fixed reference
 // equilibria: f^r_i - w_i, f^p_i, g_j - w_j, i.e. reactant liquid at rest with
-// C = 1; all arithmetic in FP32).
+// C = 1) or uint16_t (16-bit fixed point of f_i / w_i on [-0.25, 1.75)); all
+// arithmetic in FP32.
 #pragma once
 #include <cuda_fp16.h>
 
@@ -91,6 +92,38 @@ struct Store<__half> {
   }
   static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned idx, int p, float v) {
     f[idx] = half_stochastic(v - pop_ref(p), idx);
+  }
+};
+
+// 16-bit fixed point: population p is stored as q = round((f / w_p + 0.25) 2^15)
+// in [0, 65534], w_p its lattice weight (D3Q19 for f^r and f^p, D3Q7 for g), so
+// the resolution is 2^-15 w_p everywhere on f / w_p in [-0.25, 1.75) -- uniform,
+// where FP16 deviations resolve 2^-11 of |f - w| and are coarse wherever a
+// population is far from the reference (gas regions, interfaces).  Rounding is
+// stochastic (probability of rounding up = the discarded fraction; random bits
+// from the hash of half_stochastic), values outside the range saturate, and a
+// non-finite value is stored as 65535 and read back as NaN, so the observables'
+// check still finds it.
+__device__ __forceinline__ float fx_scale(int p) { return p < Q ? W[p] : (p < 2 * Q ? W[p - Q] : W7[p - 2 * Q]); }
+constexpr float kFxQuantum = 1.0f / 32768.0f;
+constexpr uint16_t kFxNaN = 0xFFFFu;
+
+template <>
+struct Store<uint16_t> {
+  static __device__ __forceinline__ float ld(const uint16_t *__restrict__ f, unsigned idx, int p) {
+    const unsigned q = f[idx];
+    const float s = fx_scale(p);
+    return q == kFxNaN ? __int_as_float(0x7fc00000) : fmaf((float)q, s * kFxQuantum, -0.25f * s);
+  }
+  static __device__ __forceinline__ void st(uint16_t *__restrict__ f, unsigned idx, int p, float v) {
+    const float qr = fmaf(v, 32768.0f / fx_scale(p), 8192.0f);
+    uint32_t h = (__float_as_uint(v) ^ idx) * 0x9E3779B9u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    const float r = (float)(h >> 8) * (1.0f / 16777216.0f);   // uniform in [0, 1)
+    const float q = fminf(fmaxf(floorf(qr + r), 0.0f), 65534.0f);
+    f[idx] = isfinite(qr) ? (uint16_t)q : kFxNaN;
   }
 };
 

@@ -44,7 +44,8 @@ def test_strerror(lib):
 def test_invalid_arguments_rejected_on_host(lib):
     solid = np.zeros((4, 4, 4), np.uint8)
     for bad in (lbm.Params(tau=0.5), lbm.Params(diffusivity=0.0), lbm.Params(reaction_mode=2),
-                lbm.Params(storage=3), lbm.Params(storage=-1), lbm.Params(rho_out=0.0)):
+                lbm.Params(storage=3), lbm.Params(storage=-1), lbm.Params(rho_out=0.0),
+                lbm.Params(storage=2, c_init=1.5), lbm.Params(storage=2, c_in=-2.0)):
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_create(solid, bad)
         assert e.value.code == lbm.LBM_EINVAL
@@ -54,6 +55,12 @@ def test_invalid_arguments_rejected_on_host(lib):
         lbm.lbm_create(np.zeros((1, 4, 4), np.uint8), lbm.Params(), bc_z=1)   # column needs nz >= 2
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create(np.zeros((4, 4, 4), np.uint8), lbm.Params(), bc_z=2)
+    # the allocation-free step takes FP32 populations only; checked before any device call
+    dummy = ctypes.c_void_p(16)
+    for st in (1, 2):
+        prm = lbm.Params(storage=st).to_c()
+        assert lib.lbm_step_static(4, 4, 4, dummy, None, dummy, ctypes.c_void_p(1 << 20), None,
+                                   ctypes.byref(prm)) == lbm.LBM_EINVAL
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_observables(None, None) == lbm.LBM_EINVAL
     lib.lbm_destroy(None)

@@ -1,11 +1,14 @@
-"""FP16 population storage (deviations from the resting reactant equilibrium).
+"""2-byte population storage with FP32 arithmetic.
 
-The stored populations are f^r - w, f^p, g - w in FP16 (stochastic rounding) with
-FP32 arithmetic.  One step from a given state must match the oracle's step up to
-one FP16 spacing of the stored output: |out - ref| <= 2^-10 |ref - f_ref| + 1e-6.
-Over a trajectory the errors against the FP64 oracle are stated as observed
-bounds: conversion and gas saturation to 1e-4 (the stated conversion error
-budget of the FP16 path), fields to the bounds written below.
+FP16 (storage 1): the stored populations are f^r - w, f^p, g - w in FP16
+(stochastic rounding).  One step from a given state must match the oracle's
+step up to one FP16 spacing of the stored output: |out - ref| <= 2^-10 |ref -
+f_ref| + 1e-6.  16-bit fixed point (storage 2): f / w on [-0.25, 1.75) in steps
+of 2^-15 (stochastic rounding), so one step matches up to one step of the
+grid, 2^-15 w + 1e-6.  Over a trajectory the errors against the FP64 oracle
+are stated as observed bounds: conversion and gas saturation to 1e-4 (the
+stated conversion error budget of the 2-byte paths), fields to the bounds
+written below.
 """
 import numpy as np
 import pytest
@@ -17,6 +20,7 @@ from paper_2608_15781_b300 import build, lbm, synth
 pytestmark = pytest.mark.gpu
 
 REF = np.concatenate([W19, np.zeros(19), W7])   # reference subtracted before FP16 storage
+SCALE = np.concatenate([W19, W19, W7])          # f / SCALE is stored in 16-bit fixed point
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -114,3 +118,94 @@ def test_fp16_stochastic_rounding_is_unbiased_and_reproducible():
         sel = (frac >= lo) & (frac < lo + 0.25)
         assert abs(up[sel].mean() - (lo + 0.125)) < 0.06, (lo, up[sel].mean())
 
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fixed16_single_step(bc):
+    shape = (12, 14, 20)
+    rng = np.random.default_rng(15 + bc)
+    solid = rng.random(shape) < 0.3
+    p = lbm.Params(sigma=0.05, theta_deg=60.0, accel=(1e-4, 0, 0), k_rate=0.05, u_in=0.01, storage=2)
+    op = _op(p, bc)
+    g = O.Geometry(solid=solid, bc_z=bc)
+    rr = rng.random(shape)
+    st = O.init_state(g, op, rho_r=rr, rho_p=1.05 - rr, conc=rng.random(shape),
+                      u=0.02 * rng.standard_normal((3,) + shape))
+    with lbm.Lattice(solid, p, bc_z=bc) as L:
+        L.set_state(st.f.astype(np.float32))
+        pre = L.get_state()            # the quantised state the GPU steps from
+        # every stored value sits on the grid (f / w + 0.25) 2^15 = integer
+        q = (pre.astype(np.float64) / SCALE[:, None, None, None] + 0.25) * 32768.0
+        assert np.abs(q - np.round(q))[:, g.fluid].max() < 1e-2
+        assert np.abs(pre - st.f)[:, g.fluid].max() <= (SCALE / 32768.0).max() + 1e-7
+        L.step(1)
+        out = L.get_state().astype(np.float64)
+    ref = O.step(O.State(f=pre.astype(np.float64)), g, op).f
+    fl = g.fluid
+    bound = np.broadcast_to((SCALE / 32768.0)[:, None, None, None], ref.shape) + 1e-6
+    bound = bound.copy()
+    if bc == 1:
+        # the planes next to the inlet and outlet also pull quantised ghost populations
+        bound[:, 0] += 2e-4
+        bound[:, -1] += 2e-4
+    assert (np.abs(out - ref) <= bound)[:, fl].all(), np.abs(out - ref)[:, fl].max()
+
+
+def test_fixed16_trajectory_errors_stated():
+    """32^3 periodic workload, 200 steps: 16-bit fixed-point storage against the FP64 oracle."""
+    shape = (32, 32, 32)
+    solid = synth.grf_mask(shape, 4, 0.55, 1)
+    p = lbm.Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=90.0, accel=(1e-6, 0.0, 0.0),
+                   diffusivity=0.05, k_rate=1e-3, c_init=1.0, storage=2)
+    op = _op(p, 0)
+    g = O.Geometry(solid=solid, bc_z=0)
+    with lbm.Lattice(solid, p) as L:
+        L.step(200)
+        out = L.get_state().astype(np.float64)
+        ob = L.observables()
+    st = O.run(O.init_state(g, op), g, op, 200)
+    oo = O.observables(st, g, op)
+    fl = g.fluid
+    assert abs(ob["conversion"] - oo["conversion"]) < 1e-4
+    assert abs(ob["gas_saturation"] - oo["gas_saturation"]) < 1e-4
+    rr = np.abs(out[0:19].sum(0) - st.f[0:19].sum(0))[fl]
+    assert np.median(rr) < 1e-4 and rr.max() < 2e-2
+
+
+def test_fixed16_rounding_unbiased_saturating_and_nan():
+    """Between two grid values a population is stored as either, with frequencies
+    matching its position; out-of-range values saturate; NaN reads back as NaN and
+    the observables report it."""
+    shape = (8, 8, 64)
+    solid = np.zeros(shape, dtype=bool)
+    p = lbm.Params(storage=2, k_rate=0.0)
+    h = W19[1] / 32768.0
+    f = np.zeros((45,) + shape, np.float32)
+    f[0:19] = W19[:, None, None, None]
+    f[38:45] = W7[:, None, None, None]
+    rng = np.random.default_rng(0)
+    frac = rng.random(shape)
+    base = W19[1] * (1.0 + 2.0 ** -10)                 # on the grid
+    f[1] = (base + frac * h).astype(np.float32)
+    with lbm.Lattice(solid, p) as L:
+        L.set_state(f)
+        a = L.get_state()
+        L.set_state(f)
+        assert np.array_equal(a, L.get_state())
+        dev = (a[1].astype(np.float64) - base) / h
+        up = np.abs(dev - 1.0) < 0.05
+        assert np.all(up | (np.abs(dev) < 0.05))
+        for lo in (0.0, 0.25, 0.5, 0.75):
+            sel = (frac >= lo) & (frac < lo + 0.25)
+            assert abs(up[sel].mean() - (lo + 0.125)) < 0.06, (lo, up[sel].mean())
+        g = f.copy()
+        g[2, 0, 0, 0] = 5.0 * W19[2]                    # above the range: saturates at 1.75 w
+        g[3, 0, 0, 1] = -1.0 * W19[3]                   # below: -0.25 w
+        g[4, 0, 0, 2] = np.nan
+        L.set_state(g)
+        b = L.get_state()
+        assert abs(b[2, 0, 0, 0] - (65534 / 32768.0 - 0.25) * W19[2]) < 1e-7
+        assert abs(b[3, 0, 0, 1] + 0.25 * W19[3]) < 1e-7
+        assert np.isnan(b[4, 0, 0, 2])
+        ob = L.observables(allow_nan=True)
+        assert ob["n_bad"] >= 1

@@ -93,9 +93,10 @@ typedef struct {
                             1: delta = min(xi NN r, 1) rho^r, C not evolved                  */
   int32_t storage;    /* population storage (FP32 arithmetic in every case): 0 = FP32;
                          1 = FP16 deviations from the resting reactant equilibrium
-                         (f^r - w, f^p, g - w); 2 = 16-bit fixed point of f / w on
-                         [-0.25, 1.75) (w the lattice weight; saturates outside; needs
-                         |c_init|, |c_in| <= 1.25).  1 and 2 round stochastically.      */
+                         (f^r - w, f^p, g - w); 2 = anchored FP16: f / w (w the
+                         lattice weight) as its deviation from the nearer of 0 and 1,
+                         9 mantissa bits plus the anchor bit.  1 and 2 round
+                         stochastically.                                              */
   void *cuda_stream;  /* cudaStream_t to launch on (borrowed); NULL = legacy default stream  */
 } lbm_params;
 

@@ -36,7 +36,7 @@ struct Batch {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool half = false;                  // 2-byte population storage (storage 1 or 2)
-  int storage = 0;                    // 0 FP32, 1 FP16 deviations, 2 16-bit fixed point
+  int storage = 0;                    // 0 FP32, 1 FP16 deviations, 2 anchored FP16
   int n = 0;
   std::vector<InstHost> h;
   // slot space
@@ -171,8 +171,6 @@ int check_params(const lbm_params *p) {
   if (!(p->beta >= 0.0) || !std::isfinite(p->sigma) || !std::isfinite(p->theta_deg)) return LBM_EINVAL;
   if (p->reaction_mode != 0 && p->reaction_mode != 1) return LBM_EINVAL;
   if (p->storage < 0 || p->storage > 2) return LBM_EINVAL;
-  // 16-bit fixed point covers g / w = C (1 + 4 c.u) up to 1.75
-  if (p->storage == 2 && (!(std::fabs(p->c_init) <= 1.25) || !(std::fabs(p->c_in) <= 1.25))) return LBM_EINVAL;
   if (!(p->k_rate >= 0.0) || !(p->xi >= 0.0) || !(p->rho_out > 0.0)) return LBM_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->accel[a])) return LBM_EINVAL;

@@ -21,7 +21,7 @@
 //
 // Storage type T: float (FP32), __half (FP16 deviations from fixed reference
 // equilibria: f^r_i - w_i, f^p_i, g_j - w_j, i.e. reactant liquid at rest with
-// C = 1) or uint16_t (16-bit fixed point of f_i / w_i on [-0.25, 1.75)); all
+// C = 1) or uint16_t (anchored FP16 of f_i / w_i, see Store<uint16_t>); all
 // arithmetic in FP32.
 #pragma once
 #include <cuda_fp16.h>
@@ -95,35 +95,35 @@ struct Store<__half> {
   }
 };
 
-// 16-bit fixed point: population p is stored as q = round((f / w_p + 0.25) 2^15)
-// in [0, 65534], w_p its lattice weight (D3Q19 for f^r and f^p, D3Q7 for g), so
-// the resolution is 2^-15 w_p everywhere on f / w_p in [-0.25, 1.75) -- uniform,
-// where FP16 deviations resolve 2^-11 of |f - w| and are coarse wherever a
-// population is far from the reference (gas regions, interfaces).  Rounding is
-// stochastic (probability of rounding up = the discarded fraction; random bits
-// from the hash of half_stochastic), values outside the range saturate, and a
-// non-finite value is stored as 65535 and read back as NaN, so the observables'
-// check still finds it.
-__device__ __forceinline__ float fx_scale(int p) { return p < Q ? W[p] : (p < 2 * Q ? W[p - Q] : W7[p - 2 * Q]); }
-constexpr float kFxQuantum = 1.0f / 32768.0f;
-constexpr uint16_t kFxNaN = 0xFFFFu;
+// Anchored FP16: population p is stored as v = f / w_p (w_p its lattice weight:
+// D3Q19 for f^r and f^p, D3Q7 for g) split into the nearer anchor a in {0, 1}
+// and the deviation d = v - a; d is an FP16 value whose lowest mantissa bit is
+// replaced by a (9 mantissa bits left).  Near either anchor -- a population of the
+// liquid or of the gas, f^r ~ w or ~ 0, f^p ~ 0 or ~ w, C ~ 1 or ~ 0 -- the
+// stored deviation is small and resolved to 2^-10 of itself; fixed-reference FP16
+// deviations (storage 1) resolve f^r - w and f^p to 2^-11 of a value of order w
+// wherever the phase is the other one.  Rounding is stochastic on the 14 discarded
+// float mantissa bits (random bits from the hash of half_stochastic); NaN stays NaN.
+__device__ __forceinline__ float anc_scale(int p) { return p < Q ? W[p] : (p < 2 * Q ? W[p - Q] : W7[p - 2 * Q]); }
 
 template <>
 struct Store<uint16_t> {
   static __device__ __forceinline__ float ld(const uint16_t *__restrict__ f, unsigned idx, int p) {
-    const unsigned q = f[idx];
-    const float s = fx_scale(p);
-    return q == kFxNaN ? __int_as_float(0x7fc00000) : fmaf((float)q, s * kFxQuantum, -0.25f * s);
+    const unsigned u = f[idx];
+    const float d = __half2float(__ushort_as_half((unsigned short)(u & 0xFFFEu)));
+    return (d + (float)(u & 1u)) * anc_scale(p);
   }
   static __device__ __forceinline__ void st(uint16_t *__restrict__ f, unsigned idx, int p, float v) {
-    const float qr = fmaf(v, 32768.0f / fx_scale(p), 8192.0f);
-    uint32_t h = (__float_as_uint(v) ^ idx) * 0x9E3779B9u;
+    const float x = v * (1.0f / anc_scale(p));
+    const unsigned a = x > 0.5f ? 1u : 0u;
+    const float d = x - (float)a;
+    const uint32_t bits = __float_as_uint(d);
+    uint32_t h = (bits ^ idx) * 0x9E3779B9u;
     h ^= h >> 15;
     h *= 0x2C1B3C6Du;
     h ^= h >> 12;
-    const float r = (float)(h >> 8) * (1.0f / 16777216.0f);   // uniform in [0, 1)
-    const float q = fminf(fmaxf(floorf(qr + r), 0.0f), 65534.0f);
-    f[idx] = isfinite(qr) ? (uint16_t)q : kFxNaN;
+    const unsigned short hb = __half_as_ushort(__float2half_rz(__uint_as_float(bits + (h >> 18))));
+    f[idx] = (uint16_t)((hb & 0xFFFEu) | a);
   }
 };
 

@@ -44,8 +44,7 @@ def test_strerror(lib):
 def test_invalid_arguments_rejected_on_host(lib):
     solid = np.zeros((4, 4, 4), np.uint8)
     for bad in (lbm.Params(tau=0.5), lbm.Params(diffusivity=0.0), lbm.Params(reaction_mode=2),
-                lbm.Params(storage=3), lbm.Params(storage=-1), lbm.Params(rho_out=0.0),
-                lbm.Params(storage=2, c_init=1.5), lbm.Params(storage=2, c_in=-2.0)):
+                lbm.Params(storage=3), lbm.Params(storage=-1), lbm.Params(rho_out=0.0)):
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_create(solid, bad)
         assert e.value.code == lbm.LBM_EINVAL

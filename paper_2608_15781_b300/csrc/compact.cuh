@@ -76,13 +76,18 @@ struct Store<float> {
 // rounding is deterministic and reproducible.  In the FP16 normal range the 13
 // discarded mantissa bits receive 13 random bits before truncation; below it (values
 // under 6.1e-5, spacing 6e-8) the rounding leans toward zero by less than one spacing.
-__device__ __forceinline__ __half half_stochastic(float x, unsigned idx) {
-  const uint32_t bits = __float_as_uint(x);
+// Non-finite values get no random bits: added to a NaN pattern such as 0x7fffffff
+// they would carry into the sign bit and store a NaN as -0.
+__device__ __forceinline__ uint32_t round_bits(uint32_t bits, unsigned idx) {
   uint32_t h = (bits ^ idx) * 0x9E3779B9u;
   h ^= h >> 15;
   h *= 0x2C1B3C6Du;
   h ^= h >> 12;
-  return __float2half_rz(__uint_as_float(bits + (h >> 19)));
+  return (bits & 0x7f800000u) == 0x7f800000u ? 0u : h;
+}
+__device__ __forceinline__ __half half_stochastic(float x, unsigned idx) {
+  const uint32_t bits = __float_as_uint(x);
+  return __float2half_rz(__uint_as_float(bits + (round_bits(bits, idx) >> 19)));
 }
 
 template <>
@@ -118,11 +123,8 @@ struct Store<uint16_t> {
     const unsigned a = x > 0.5f ? 1u : 0u;
     const float d = x - (float)a;
     const uint32_t bits = __float_as_uint(d);
-    uint32_t h = (bits ^ idx) * 0x9E3779B9u;
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    const unsigned short hb = __half_as_ushort(__float2half_rz(__uint_as_float(bits + (h >> 18))));
+    const unsigned short hb =
+        __half_as_ushort(__float2half_rz(__uint_as_float(bits + (round_bits(bits, idx) >> 18))));
     f[idx] = (uint16_t)((hb & 0xFFFEu) | a);
   }
 };

@@ -109,6 +109,11 @@ def test_fp16_stochastic_rounding_is_unbiased_and_reproducible():
         a = L.get_state()
         L.set_state(f)
         b = L.get_state()
+        g = f.copy()
+        g[4, 0, 0, 2] = np.nan                   # a NaN stays a NaN and the observables see it
+        L.set_state(g)
+        assert np.isnan(L.get_state()[4, 0, 0, 2])
+        assert L.observables(allow_nan=True)["n_bad"] >= 1
     assert np.array_equal(a, b)
     dev = a[1].astype(np.float64) - W19[1] - 2.0 ** -7
     up = np.isclose(dev, h, atol=h / 8)

@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--storage", choices=("fp32", "fp16", "afp16"), default="fp32",
+    ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",
                     help="population storage of the headline run (the other is reported under variants)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="T",
@@ -182,13 +182,13 @@ def bytes_per_fluid_node(params):
     """Algorithmic bytes of one fluid-node update: populations read + written, plus 1 B of flags.
 
     FP32 storage: 361 B with the reactant populations (45 values each way), 305 B
-    in the paper's reaction mode (38); 2-byte storage (FP16 or anchored FP16): 181 B / 153 B.  Solid nodes
+    in the paper's reaction mode (38); FP16 storage: 181 B / 153 B.  Solid nodes
     carry no populations (the library
     stores the fluid nodes only), so a launch's algorithmic traffic is this
     figure times the number of fluid nodes.
     """
     npop = 45 if params.reaction_mode == 0 else 38
-    width = 2 if params.storage in (1, 2) else 4
+    width = 2 if params.storage == 1 else 4
     return 2 * width * npop + 1
 
 
@@ -325,7 +325,7 @@ def run_native(args):
     peak, peak_kind = measured_peaks()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
-    head = dataclasses.replace(wl.params, storage={"fp32": 0, "fp16": 1, "afp16": 2}[args.storage])
+    head = dataclasses.replace(wl.params, storage={"fp32": 0, "fp16": 1}[args.storage])
     t_ms, prof, info, ob, clk = measure(head, args.steps, args.warmup, ClockSampler(gpu_idx))
     Nf = info["n_fluid"]
     value = whole_job_mlups(world, N, args.steps, t_ms)
@@ -365,9 +365,8 @@ def run_native(args):
     variants = {}
     if not args.no_variants:
         vsteps = max(args.steps // 2, 1)
-        names = {0: ("fp32_storage", "f32"), 1: ("fp16_storage", "f16 storage, f32 math"),
-                 2: ("afp16_storage", "anchored FP16 storage, f32 math")}
-        for st in (0, 1, 2):
+        names = {0: ("fp32_storage", "f32"), 1: ("fp16_storage", "f16 storage, f32 math")}
+        for st in (0, 1):
             if st == head.storage:
                 continue
             other = dataclasses.replace(head, storage=st)
@@ -395,13 +394,13 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": ["f32", "f16 storage, f32 math", "anchored FP16 storage, f32 math"][head.storage],
+        "scaling": "weak", "vs_baseline": None, "dtype": ["f32", "f16 storage, f32 math"][head.storage],
         "data": "synthetic",
         "config": {"workload": wl.name, "lattice_xyz": [wl.shape[2], wl.shape[1], wl.shape[0]],
                    "mask": f"GRF shell |k|={wl.shell_k0}+-1, porosity {wl.porosity}, seed {wl.seed}",
                    "fluid_nodes": Nf, "porosity": round(Nf / N, 4),
                    "boundaries": "inlet/outlet in z" if wl.bc_z else "periodic",
-                   "storage": ["fp32", "fp16 deviations", "anchored fp16 of f/w"][head.storage],
+                   "storage": ["fp32", "fp16 deviations"][head.storage],
                    "fluid_mlups": round(world * Nf * args.steps / (t_ms * 1e-3) / 1e6, 2),
                    "l2": "state (2 x 45 x fluid nodes x 4 B) far above the 126 MB L2; no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
@@ -504,9 +503,9 @@ def velocity_difference(fa, fb, solid, chunk=16):
 
 
 def measure_precision(lbm, torch, stream, world, nsteps):
-    """256^3 periodic workload: FP32, FP16 and anchored-FP16 population storage from
-    the same start, MLUPS of each and the differences of conversion, gas saturation and u
-    against FP32, next to the spread of two FP32 runs from starts 1e-6 apart."""
+    """256^3 periodic workload: FP32 and FP16 population storage from the same start,
+    MLUPS of each and the FP16 - FP32 differences of conversion, gas saturation and u,
+    next to the spread of two FP32 runs from starts 1e-6 apart."""
     from paper_2608_15781_b300.configs import WORKLOADS
 
     wl = WORKLOADS["periodic256"]
@@ -519,7 +518,6 @@ def measure_precision(lbm, torch, stream, world, nsteps):
     n_bad = 0
     for name, storage, rho_r in (("fp32", 0, np.ones(solid.shape, np.float32)),
                                  ("fp16", 1, np.ones(solid.shape, np.float32)),
-                                 ("afp16", 2, np.ones(solid.shape, np.float32)),
                                  ("fp32_spread_1e-6_start", 0, perturbed)):
         L = lbm.Lattice(solid, dataclasses.replace(wl.params, storage=storage), bc_z=0, stream=stream.cuda_stream)
         L.step(3)

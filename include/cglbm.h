@@ -91,12 +91,8 @@ typedef struct {
   double xi;          /* reaction rate of the paper's mode (Eq. reactive_boundary_condition_*) */
   int32_t reaction_mode; /* 0: delta = min(k NN r C psi, C, rho^r), C on D3Q7;
                             1: delta = min(xi NN r, 1) rho^r, C not evolved                  */
-  int32_t storage;    /* population storage (FP32 arithmetic in every case): 0 = FP32;
-                         1 = FP16 deviations from the resting reactant equilibrium
-                         (f^r - w, f^p, g - w); 2 = anchored FP16: f / w (w the
-                         lattice weight) as its deviation from the nearer of 0 and 1,
-                         9 mantissa bits plus the anchor bit.  1 and 2 round
-                         stochastically.                                              */
+  int32_t storage;    /* population storage: 0 = FP32; 1 = FP16 deviations from the resting
+                         reactant equilibrium (f^r - w, f^p, g - w), FP32 arithmetic          */
   void *cuda_stream;  /* cudaStream_t to launch on (borrowed); NULL = legacy default stream  */
 } lbm_params;
 

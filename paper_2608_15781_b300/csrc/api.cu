@@ -35,8 +35,7 @@ struct InstHost {
 struct Batch {
   int device = 0;
   cudaStream_t stream = nullptr;
-  bool half = false;                  // 2-byte population storage (storage 1 or 2)
-  int storage = 0;                    // 0 FP32, 1 FP16 deviations, 2 anchored FP16
+  bool half = false;                  // FP16 deviation storage
   int n = 0;
   std::vector<InstHost> h;
   // slot space
@@ -170,7 +169,7 @@ int check_params(const lbm_params *p) {
   if (!(p->diffusivity > 0.0) || !std::isfinite(p->diffusivity)) return LBM_EINVAL;
   if (!(p->beta >= 0.0) || !std::isfinite(p->sigma) || !std::isfinite(p->theta_deg)) return LBM_EINVAL;
   if (p->reaction_mode != 0 && p->reaction_mode != 1) return LBM_EINVAL;
-  if (p->storage < 0 || p->storage > 2) return LBM_EINVAL;
+  if (p->storage != 0 && p->storage != 1) return LBM_EINVAL;
   if (!(p->k_rate >= 0.0) || !(p->xi >= 0.0) || !(p->rho_out > 0.0)) return LBM_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->accel[a])) return LBM_EINVAL;
@@ -220,9 +219,7 @@ Lattice make_lattice(const lbm_geometry &g) {
 // run f((T *)nullptr) with T the batch's population storage type
 template <class F>
 void with_storage(const Batch &b, F &&f) {
-  if (b.storage == 2)
-    f((uint16_t *)nullptr);
-  else if (b.storage == 1)
+  if (b.half)
     f((__half *)nullptr);
   else
     f((float *)nullptr);
@@ -492,8 +489,7 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   }
   cudaGetDevice(&b.device);
   b.stream = (cudaStream_t)stream;
-  b.storage = params[0].storage;
-  b.half = b.storage != 0;
+  b.half = params[0].storage == 1;
   b.n = n;
   b.h.resize(n);
   // per-instance node / gidx offsets and static geometry

@@ -19,10 +19,9 @@
 // at the instance's node offset; gidx maps each stored lattice position
 // (plane z + 1 in [0, nz + 1]) to a global slot, or -1 for a solid node.
 //
-// Storage type T: float (FP32), __half (FP16 deviations from fixed reference
+// Storage type T: float (FP32) or __half (FP16 deviations from fixed reference
 // equilibria: f^r_i - w_i, f^p_i, g_j - w_j, i.e. reactant liquid at rest with
-// C = 1) or uint16_t (anchored FP16 of f_i / w_i, see Store<uint16_t>); all
-// arithmetic in FP32.
+// C = 1; all arithmetic in FP32).
 #pragma once
 #include <cuda_fp16.h>
 
@@ -97,35 +96,6 @@ struct Store<__half> {
   }
   static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned idx, int p, float v) {
     f[idx] = half_stochastic(v - pop_ref(p), idx);
-  }
-};
-
-// Anchored FP16: population p is stored as v = f / w_p (w_p its lattice weight:
-// D3Q19 for f^r and f^p, D3Q7 for g) split into the nearer anchor a in {0, 1}
-// and the deviation d = v - a; d is an FP16 value whose lowest mantissa bit is
-// replaced by a (9 mantissa bits left).  Near either anchor -- a population of the
-// liquid or of the gas, f^r ~ w or ~ 0, f^p ~ 0 or ~ w, C ~ 1 or ~ 0 -- the
-// stored deviation is small and resolved to 2^-10 of itself; fixed-reference FP16
-// deviations (storage 1) resolve f^r - w and f^p to 2^-11 of a value of order w
-// wherever the phase is the other one.  Rounding is stochastic on the 14 discarded
-// float mantissa bits (random bits from the hash of half_stochastic); NaN stays NaN.
-__device__ __forceinline__ float anc_scale(int p) { return p < Q ? W[p] : (p < 2 * Q ? W[p - Q] : W7[p - 2 * Q]); }
-
-template <>
-struct Store<uint16_t> {
-  static __device__ __forceinline__ float ld(const uint16_t *__restrict__ f, unsigned idx, int p) {
-    const unsigned u = f[idx];
-    const float d = __half2float(__ushort_as_half((unsigned short)(u & 0xFFFEu)));
-    return (d + (float)(u & 1u)) * anc_scale(p);
-  }
-  static __device__ __forceinline__ void st(uint16_t *__restrict__ f, unsigned idx, int p, float v) {
-    const float x = v * (1.0f / anc_scale(p));
-    const unsigned a = x > 0.5f ? 1u : 0u;
-    const float d = x - (float)a;
-    const uint32_t bits = __float_as_uint(d);
-    const unsigned short hb =
-        __half_as_ushort(__float2half_rz(__uint_as_float(bits + (round_bits(bits, idx) >> 18))));
-    f[idx] = (uint16_t)((hb & 0xFFFEu) | a);
   }
 };
 

@@ -293,6 +293,8 @@ def run_native(args):
         L = lbm.Lattice(solid, params, bc_z=wl.bc_z, stream=stream.cuda_stream)
         info = L.info()
         L.step(warmup)
+        info["launch"] = L.tune()     # the library's launch-shape tuner, on the warmed-up state
+        L.step(warmup)
         barrier()
         if clocks:
             clocks.start()
@@ -402,6 +404,7 @@ def run_native(args):
                    "boundaries": "inlet/outlet in z" if wl.bc_z else "periodic",
                    "storage": ["fp32", "fp16 deviations"][head.storage],
                    "fluid_mlups": round(world * Nf * args.steps / (t_ms * 1e-3) / 1e6, 2),
+                   "launch_shapes": info["launch"],
                    "l2": "state (2 x 45 x fluid nodes x 4 B) far above the 126 MB L2; no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": f"k_{kname}", "achieved": round(achieved, 1), "peak": peak,

@@ -179,15 +179,18 @@ int lbm_set_debug(lbm_ctx *ctx, int32_t enable);
 int lbm_profile(lbm_ctx *ctx, int32_t enable);
 int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
-/* Launch shapes of the step (not part of the paper): lbm_tune times each
+/* Launch configuration of the step (not part of the paper): lbm_tune times each
  * candidate on the current state (main kernel 64/128/256 threads; colour-function
- * and normal kernels 128/256/512) and keeps the fastest; blocks[3] (may be NULL)
- * receives the choice (main, density, normal).  The state is not advanced.
- * Without a call the defaults (128, 256, 256) are used. */
+ * and normal kernels 128/256/512; then whole steps with the four kernels after
+ * the first launched as programmatic dependent launches, which lets each one be
+ * scheduled while its predecessor's last blocks run, or as plain launches) and
+ * keeps the fastest; blocks[4] (may be NULL) receives the choice (main, density,
+ * normal, programmatic 1 / plain 0).  Every choice gives bit-identical results.
+ * The state is not advanced.  Without a call: 128, 256, 256, 1. */
 int lbm_tune(lbm_ctx *ctx, int32_t *blocks);
 
-/* Set the launch shapes directly (blocks[3] as filled by lbm_tune, e.g. a tuning
- * saved earlier).  LBM_EINVAL for a value outside the candidates.  The next step
+/* Set the launch configuration directly (blocks[4] as filled by lbm_tune, e.g. a
+ * tuning saved earlier).  LBM_EINVAL for a value outside the candidates.  The next step
  * rebuilds the step's CUDA graphs. */
 int lbm_set_launch(lbm_ctx *ctx, const int32_t *blocks);
 

@@ -62,6 +62,7 @@ struct Batch {
   int sticky = LBM_OK;
   // launch shapes (lbm_tune picks them by timing)
   int main_block = 128, dens_block = 256, norm_block = 256;
+  bool pdl = true;                    // programmatic dependent launch of the step's kernels 2-5
   // CUDA graphs of one step, for even and odd steps
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graphs_valid = false;
@@ -227,6 +228,29 @@ void with_storage(const Batch &b, F &&f) {
 
 Slots slots(const Batch &b) { return Slots{b.inst, b.kid, b.node, b.nslots, b.ns}; }
 
+// Launch of a step kernel that follows another step kernel on the same stream:
+// with pdl, as a programmatic dependent launch (the kernel itself waits for its
+// predecessor in pdl_begin), else a plain launch.
+template <typename... KArgs, typename... Args>
+void launch_step_kernel(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                        Args... args) {
+  if (!pdl) {
+    k<<<grid, block, 0, st>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <typename T, bool BT>
 void launch_density_t(const Batch &b, cudaStream_t st, const void *fin) {
   const Slots S = slots(b);
@@ -254,10 +278,19 @@ template <bool BT>
 void launch_normal_t(const Batch &b, cudaStream_t st) {
   const Slots S = slots(b);
   const Inst &I = b.h[0].d;
+  const float *rn = b.rhoN;
+  const uint32_t *lk = b.link;
+  const float4 *nsv = b.nsv;
+  float4 *nrm = b.nrm;
   switch (b.norm_block) {
-    case 128: k_normal_c<128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, b.nrm); break;
-    case 512: k_normal_c<512, BT><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, b.nrm); break;
-    default: k_normal_c<256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, b.nrm);
+    case 128:
+      launch_step_kernel(b.pdl, k_normal_c<128, BT>, (S.nslots + 127) / 128, 128, st, S, I, rn, lk, nsv, nrm);
+      break;
+    case 512:
+      launch_step_kernel(b.pdl, k_normal_c<512, BT>, (S.nslots + 511) / 512, 512, st, S, I, rn, lk, nsv, nrm);
+      break;
+    default:
+      launch_step_kernel(b.pdl, k_normal_c<256, BT>, (S.nslots + 255) / 256, 256, st, S, I, rn, lk, nsv, nrm);
   }
 }
 void launch_normal(const Batch &b, cudaStream_t st) {
@@ -272,18 +305,24 @@ void launch_main_t(const Batch &b, cudaStream_t st, const void *fin, void *fout,
   const Slots S = slots(b);
   const Inst &I = b.h[0].d;
   float *dh = b.debug ? b.dbg_H : nullptr, *dd = b.debug ? b.dbg_delta : nullptr;
+  const T *fi = (const T *)fin;
+  T *fo = (T *)fout;
+  const int *gi = b.gidx;
+  const uint32_t *lk = b.link;
+  const float4 *nrm = b.nrm;
+  const int n = b.n;
   switch (b.main_block) {
     case 64:
-      k_main_c<T, 64, BT><<<(S.nslots + 63) / 64, 64, 0, st>>>(S, I, b.n, (const T *)fin, (T *)fout, b.gidx, b.link,
-                                                              b.nrm, acc, slot, dh, dd);
+      launch_step_kernel(b.pdl, k_main_c<T, 64, BT>, (S.nslots + 63) / 64, 64, st, S, I, n, fi, fo, gi, lk, nrm, acc,
+                         slot, dh, dd);
       break;
     case 256:
-      k_main_c<T, 256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, b.n, (const T *)fin, (T *)fout, b.gidx,
-                                                                  b.link, b.nrm, acc, slot, dh, dd);
+      launch_step_kernel(b.pdl, k_main_c<T, 256, BT>, (S.nslots + 255) / 256, 256, st, S, I, n, fi, fo, gi, lk, nrm,
+                         acc, slot, dh, dd);
       break;
     default:
-      k_main_c<T, 128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, b.n, (const T *)fin, (T *)fout, b.gidx,
-                                                                  b.link, b.nrm, acc, slot, dh, dd);
+      launch_step_kernel(b.pdl, k_main_c<T, 128, BT>, (S.nslots + 127) / 128, 128, st, S, I, n, fi, fo, gi, lk, nrm,
+                         acc, slot, dh, dd);
   }
 }
 template <typename T>
@@ -296,18 +335,21 @@ void launch_main(const Batch &b, cudaStream_t st, const void *fin, void *fout, d
 
 void launch_solids(const Batch &b, cudaStream_t st, bool colour) {
   const Inst &I = b.h[0].d;
-  const unsigned g = (unsigned)((b.n_bnd + 127) / 128);
+  const unsigned g = (unsigned)((b.n_bnd + 127) / 128), g256 = (unsigned)((b.n_bnd + 255) / 256);
+  const Inst *in = b.inst;
+  const uint32_t *bnd = b.bnd, *lk = b.link;
+  const uint16_t *bk = b.bnd_kid;
+  const int nb = b.n_bnd;
   if (colour) {
     if (b.n > 1)
-      k_color_solid_c<true><<<g, 128, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+      launch_step_kernel(b.pdl, k_color_solid_c<true>, g, 128, st, in, I, bnd, bk, nb, lk, b.rhoN);
     else
-      k_color_solid_c<false><<<g, 128, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.rhoN);
+      launch_step_kernel(b.pdl, k_color_solid_c<false>, g, 128, st, in, I, bnd, bk, nb, lk, b.rhoN);
   } else {
-    const unsigned g256 = (unsigned)((b.n_bnd + 255) / 256);
     if (b.n > 1)
-      k_normal_solid_c<true><<<g256, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+      launch_step_kernel(b.pdl, k_normal_solid_c<true>, g256, 256, st, in, I, bnd, bk, nb, lk, b.nrm);
     else
-      k_normal_solid_c<false><<<g256, 256, 0, st>>>(b.inst, I, b.bnd, b.bnd_kid, b.n_bnd, b.link, b.nrm);
+      launch_step_kernel(b.pdl, k_normal_solid_c<false>, g256, 256, st, in, I, bnd, bk, nb, lk, b.nrm);
   }
 }
 
@@ -842,6 +884,18 @@ int tune(Batch &b, int32_t *chosen) {
     }
   }
   b.norm_block = pick;
+  // programmatic dependent launch of the step's later kernels, on or off, over whole steps
+  best = 1e30f;
+  bool pick_pdl = b.pdl;
+  for (int v = 1; v >= 0; --v) {
+    b.pdl = v == 1;
+    const float t = time_it([&] { enqueue_step(b, b.stream, b.fa, b.fb, 0, false, b.acc_scratch); });
+    if (t < best) {
+      best = t;
+      pick_pdl = b.pdl;
+    }
+  }
+  b.pdl = pick_pdl;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
@@ -851,6 +905,7 @@ int tune(Batch &b, int32_t *chosen) {
     chosen[0] = b.main_block;
     chosen[1] = b.dens_block;
     chosen[2] = b.norm_block;
+    chosen[3] = b.pdl ? 1 : 0;
   }
   return LBM_OK;
 }
@@ -858,11 +913,13 @@ int tune(Batch &b, int32_t *chosen) {
 int set_launch(Batch &b, const int32_t *blocks) {
   if (!blocks) return LBM_EINVAL;
   const auto one_of = [](int v, int a, int c, int d) { return v == a || v == c || v == d; };
-  if (!one_of(blocks[0], 64, 128, 256) || !one_of(blocks[1], 128, 256, 512) || !one_of(blocks[2], 128, 256, 512))
+  if (!one_of(blocks[0], 64, 128, 256) || !one_of(blocks[1], 128, 256, 512) || !one_of(blocks[2], 128, 256, 512) ||
+      (blocks[3] != 0 && blocks[3] != 1))
     return LBM_EINVAL;
   b.main_block = blocks[0];
   b.dens_block = blocks[1];
   b.norm_block = blocks[2];
+  b.pdl = blocks[3] == 1;
   drop_graphs(b);
   return LBM_OK;
 }

@@ -168,6 +168,18 @@ __device__ __forceinline__ void block_delta_inst(double d, int k, double *acc, i
   }
 }
 
+// Programmatic dependent launch of the step's kernels: let the next kernel of the
+// step be scheduled now (its blocks take the SM slots that this grid's last wave
+// frees), then wait until the kernel before this one has completed and its writes
+// are visible.  Called first thing by every step kernel, before any early return,
+// so a grid completes only after its predecessor did, and so on back to the first
+// kernel of the step.  Both instructions are no-ops for a launch without the
+// programmatic attribute.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // pull of the 45 (38) populations of fluid slot t at (x, y, z), halfway bounce-back
 // where the source is solid (gidx < 0)
 template <typename T>
@@ -213,6 +225,7 @@ template <typename T, int BLOCK, bool BATCH>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, const __grid_constant__ Inst single,
                                                      const T *__restrict__ f, const int *__restrict__ gidx,
                                                      float *__restrict__ rhoN) {
+  pdl_begin();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)S.nslots) return;
   const uint32_t pk = S.node[t];
@@ -242,6 +255,7 @@ template <int BLOCK, bool BATCH>
 __global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const __grid_constant__ Inst single,
                                                     const float *__restrict__ rhoN, const uint32_t *__restrict__ link,
                                                     const float4 *__restrict__ ns, float4 *__restrict__ nrm) {
+  pdl_begin();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)S.nslots) return;
   const uint32_t pk = S.node[t];
@@ -277,6 +291,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(128) k_color_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
                                 const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
                                 const uint32_t *__restrict__ link, float *__restrict__ rhoN) {
+  pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const Inst &I = BATCH ? inst[kid[t]] : single;
@@ -303,6 +318,7 @@ template <bool BATCH>
 __global__ void k_normal_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
                                  const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
                                  const uint32_t *__restrict__ link, float4 *__restrict__ nrm) {
+  pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const Inst &I = BATCH ? inst[kid[t]] : single;
@@ -371,6 +387,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
                                                                const float4 *__restrict__ nrm, double *__restrict__ acc,
                                                                int slot, float *__restrict__ dbg_H,
                                                                float *__restrict__ dbg_delta) {
+  pdl_begin();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x == 0) {
     if (BATCH) {

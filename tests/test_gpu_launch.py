@@ -1,6 +1,7 @@
-"""Launch shapes of the step: every choice lbm_tune can make gives the same
+"""Launch configurations of the step: every choice lbm_tune can make (block
+sizes, programmatic dependent launch or plain launches) gives the same
 populations bit for bit, for one lattice and for a batch, FP32 and FP16
-storage; bad shapes are rejected; the tuner keeps the state."""
+storage; bad configurations are rejected; the tuner keeps the state."""
 import dataclasses
 
 import numpy as np
@@ -10,7 +11,7 @@ from paper_2608_15781_b300 import build, lbm, synth
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(main=128, density=256, normal=256)
+DEFAULT = dict(main=128, density=256, normal=256, pdl=1)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -45,7 +46,8 @@ def test_launch_choices_are_bit_identical(bc, storage):
     solid, p, rr, rp = _case(bc, storage)
     f0, ob0 = _run(solid, p, bc, rr, rp, DEFAULT)
     assert ob0["n_bad"] == 0
-    for launch in (dict(main=64, density=128, normal=512), dict(main=256, density=512, normal=128)):
+    for launch in (dict(DEFAULT, pdl=0), dict(main=64, density=128, normal=512, pdl=1),
+                   dict(main=256, density=512, normal=128, pdl=0)):
         f1, ob1 = _run(solid, p, bc, rr, rp, launch)
         assert np.array_equal(f0, f1), launch
         assert ob1["mass_r"] == ob0["mass_r"] and ob1["gas_saturation"] == ob0["gas_saturation"]
@@ -55,7 +57,7 @@ def test_batch_launch_shapes():
     masks = [synth.grf_mask((14, 12, 16), 2, 0.5, s, periodic_z=False) for s in (3, 4, 5)]
     ps = [lbm.Params(theta_deg=t, u_in=0.005, c_in=1.0, k_rate=0.01) for t in (40.0, 80.0, 110.0)]
     states = []
-    for launch in (DEFAULT, dict(main=64, density=512, normal=128)):
+    for launch in (DEFAULT, dict(main=64, density=512, normal=128, pdl=0)):
         with lbm.Batch(masks, ps, bc_z=[1, 1, 1]) as B:
             B.set_launch(launch)
             B.step(7)
@@ -67,14 +69,15 @@ def test_batch_launch_shapes():
 def test_set_launch_rejects_and_tune_reports():
     solid, p, rr, rp = _case(0, 0)
     with lbm.Lattice(solid, p) as L:
-        for bad in (dict(DEFAULT, main=96), dict(DEFAULT, density=64), dict(DEFAULT, normal=1024)):
+        for bad in (dict(DEFAULT, main=96), dict(DEFAULT, density=64), dict(DEFAULT, normal=1024),
+                    dict(DEFAULT, pdl=2)):
             with pytest.raises(lbm.LbmError):
                 L.set_launch(bad)
         L.step(2)
         st = L.get_state()
         chosen = L.tune()
         assert np.array_equal(L.get_state(), st)
-        assert chosen["main"] in (64, 128, 256) and chosen["normal"] in (128, 256, 512)
+        assert chosen["main"] in (64, 128, 256) and chosen["normal"] in (128, 256, 512) and chosen["pdl"] in (0, 1)
         L.set_launch(chosen)
         L.step(2)
         L.observables()

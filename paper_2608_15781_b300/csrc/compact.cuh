@@ -67,6 +67,9 @@ template <>
 struct Store<float> {
   static __device__ __forceinline__ float ld(const float *__restrict__ f, unsigned idx, int) { return f[idx]; }
   static __device__ __forceinline__ void st(float *__restrict__ f, unsigned idx, int, float v) { f[idx] = v; }
+  static __device__ __forceinline__ void st_r(float *__restrict__ f, unsigned idx, int, float v, uint32_t) {
+    f[idx] = v;
+  }
 };
 // FP32 -> FP16 with stochastic rounding: round away from zero with probability equal
 // to the discarded fraction of an FP16 spacing, so that per-step changes smaller than
@@ -89,6 +92,20 @@ __device__ __forceinline__ __half half_stochastic(float x, unsigned idx) {
   return __float2half_rz(__uint_as_float(bits + (round_bits(bits, idx) >> 19)));
 }
 
+// The main kernel stores 45 values per node: it hashes once per node (node_seed)
+// and gives population p the top 13 bits of seed * K_p, K_p an odd constant per
+// population -- one multiply per store instead of a hash per store.
+__device__ __forceinline__ uint32_t node_seed(float v, unsigned t) {
+  uint32_t h = (__float_as_uint(v) ^ (t * 0x85EBCA6Bu)) * 0x9E3779B9u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 13;
+  return h * 0x27D4EB2Fu;
+}
+__device__ __forceinline__ uint32_t pop_random(uint32_t seed, int p) {
+  return seed * ((0x9E3779B9u ^ ((uint32_t)p * 0x632BE5ABu)) | 1u);
+}
+
 template <>
 struct Store<__half> {
   static __device__ __forceinline__ float ld(const __half *__restrict__ f, unsigned idx, int p) {
@@ -96,6 +113,12 @@ struct Store<__half> {
   }
   static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned idx, int p, float v) {
     f[idx] = half_stochastic(v - pop_ref(p), idx);
+  }
+  // the same rounding with the random word r supplied by the caller (top 13 bits used)
+  static __device__ __forceinline__ void st_r(__half *__restrict__ f, unsigned idx, int p, float v, uint32_t r) {
+    const uint32_t bits = __float_as_uint(v - pop_ref(p));
+    const uint32_t add = (bits & 0x7f800000u) == 0x7f800000u ? 0u : (r >> 19);
+    f[idx] = __float2half_rz(__uint_as_float(bits + add));
   }
 };
 
@@ -418,15 +441,17 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     pull_compact<T>(S.ns, I.P, fin, gidx + (BATCH ? I.gidx_off : 0), O, t, fr, fp, g);
     const float delta = collide_node(I.P, lk, fr, fp, g, nme, H);
     const unsigned ns = (unsigned)S.ns;
+    const uint32_t seed = node_seed(fr[Q - 1], t);   // FP16 rounding bits (unused for FP32)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      Store<T>::st(fout, (unsigned)i * ns + t, i, fr[i]);
-      Store<T>::st(fout, (unsigned)(Q + i) * ns + t, Q + i, fp[i]);
+      Store<T>::st_r(fout, (unsigned)i * ns + t, i, fr[i], pop_random(seed, i));
+      Store<T>::st_r(fout, (unsigned)(Q + i) * ns + t, Q + i, fp[i], pop_random(seed, Q + i));
     }
     float g5;
     if (I.P.reaction_mode == 0) {
 #pragma unroll
-      for (int j = 0; j < Q7; ++j) Store<T>::st(fout, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j, g[j]);
+      for (int j = 0; j < Q7; ++j)
+        Store<T>::st_r(fout, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j, g[j], pop_random(seed, 2 * Q + j));
       g5 = g[5];
     } else {
       g5 = Store<T>::ld(fin, (unsigned)(2 * Q + 5) * ns + t, 2 * Q + 5);

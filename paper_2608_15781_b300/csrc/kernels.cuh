@@ -32,6 +32,24 @@ struct StepParams {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// c_i . (a, b, c) with only the nonzero components of c_i (+-1) entering: a product
+// with a zero component cannot be folded away (0 * x is not 0 for every x), so the
+// hot loops spell the sum out per direction.
+__device__ __forceinline__ float cdot(int i, float a, float b, float c) {
+  float s = 0.f;
+  bool any = false;
+  if (CX[i]) {
+    s = CX[i] > 0 ? a : -a;
+    any = true;
+  }
+  if (CY[i]) {
+    s = any ? (CY[i] > 0 ? s + b : s - b) : (CY[i] > 0 ? b : -b);
+    any = true;
+  }
+  if (CZ[i]) s = any ? (CZ[i] > 0 ? s + c : s - c) : (CZ[i] > 0 ? c : -c);
+  return s;
+}
+
 __device__ __forceinline__ float feq19(int i, float rho, float vx, float vy, float vz, float vv) {
   const float cu = CX[i] * vx + CY[i] * vy + CZ[i] * vz;
   return W[i] * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * vv);
@@ -535,16 +553,22 @@ __global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, lon
 
 // a6: H = -sum_ab (delta_ab - n_a n_b) d_a n_b, d_a n_b by Eq. finite_difference_scheme;
 // nb(i) returns the normal at x + c_i
+// (the 18 neighbours taken as 9 opposite pairs: c_opp = -c, so each pair adds
+// 3 w c_a (n_b(x + c) - n_b(x - c)), one difference per component instead of a
+// second product per nonzero c_a)
 template <class NbNormal>
 __device__ __forceinline__ float curvature(const float4 nme, const NbNormal &nb) {
   float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  constexpr int PAIR[9] = {0, 2, 4, 6, 7, 8, 9, 14, 15};   // i < OPP[i]
 #pragma unroll
-  for (int i = 0; i < Q - 1; ++i) {
-    const float4 v = nb(i);
+  for (int k = 0; k < 9; ++k) {
+    const int i = PAIR[k];
+    const float4 a = nb(i), b = nb(OPP[i]);
+    const float vx = a.x - b.x, vy = a.y - b.y, vz = a.z - b.z;
     const float w3 = 3.0f * W[i];
-    if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
-    if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
-    if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
+    if (CX[i]) { d[0][0] += w3 * CX[i] * vx; d[0][1] += w3 * CX[i] * vy; d[0][2] += w3 * CX[i] * vz; }
+    if (CY[i]) { d[1][0] += w3 * CY[i] * vx; d[1][1] += w3 * CY[i] * vy; d[1][2] += w3 * CY[i] * vz; }
+    if (CZ[i]) { d[2][0] += w3 * CZ[i] * vx; d[2][1] += w3 * CZ[i] * vy; d[2][2] += w3 * CZ[i] * vz; }
   }
   const float n3[3] = {nme.x, nme.y, nme.z};
   float proj = d[0][0] + d[1][1] + d[2][2];
@@ -613,20 +637,33 @@ __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, 
   // the FP32-rounded weights sum to 1 + 2.5e-8, which would otherwise add that
   // much mass per node and step.
   const float Brec = P.beta * rr * rp * inv_rho;
+  // Node-level factors first, so that each direction costs a few operations:
+  // f^eq_i = w_i rho (A + c.u (3 + 4.5 c.u)), A = 1 - 1.5 u.u, and the recolouring
+  // and reaction term w_i (Brec cos(phi_i) - delta) = +-b_a +- b_b - w_i delta with
+  // b = w_i Brec n / |c_i| for the axis (|c| = 1) and diagonal (|c| = sqrt 2) classes.
+  const float A = 1.0f - 1.5f * vv;
+  const float wr1 = W1 * rho, wr2 = W2 * rho;
+  const float b1 = W1 * Brec, b2 = W2 * Brec * RSQRT2;
+  const float b1x = b1 * nme.x, b1y = b1 * nme.y, b1z = b1 * nme.z;
+  const float b2x = b2 * nme.x, b2y = b2 * nme.y, b2z = b2 * nme.z;
+  const float d1 = W1 * delta, d2 = W2 * delta;
   float msum = 0.f;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    float fm_star;
-    if (i < Q - 1) {
-      fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
-      msum += fm_star;
-    } else {
-      fm_star = rho - msum;
-    }
-    const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
-    const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
+  for (int i = 0; i < Q - 1; ++i) {
+    const bool axis = i < 6;
+    const float cu = cdot(i, vx, vy, vz);
+    const float fm_star = (axis ? wr1 : wr2) * fmaf(cu, fmaf(4.5f, cu, 3.0f), A) + bt[i];
+    msum += fm_star;
+    const float rec = axis ? cdot(i, b1x, b1y, b1z) - d1 : cdot(i, b2x, b2y, b2z) - d2;
+    const float r_star = fmaf(psi, fm_star, rec);
     fr[i] = r_star;
     fp[i] = fm_star - r_star;
+  }
+  {
+    const float fm_star = rho - msum;   // rest population: cos(phi) = 0
+    const float r_star = fmaf(psi, fm_star, -W0 * delta);
+    fr[Q - 1] = r_star;
+    fp[Q - 1] = fm_star - r_star;
   }
   if (P.reaction_mode == 0) {
     // D3Q7 BGK of C advected by the physical velocity u + du/2, minus the reacted amount

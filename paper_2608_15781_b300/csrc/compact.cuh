@@ -25,6 +25,8 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace cglbm {
@@ -433,13 +435,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     const float4 *nn = nrm + noff;
     const uint32_t lk = link[noff + node];
     const float4 nme = nn[node];
+    constexpr bool LEAN = std::is_same<T, __half>::value;
     const float H =
-        nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nn[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
+        nme.w >= GRAD_EPS ? curvature<LEAN>(nme, [&](int i) { return nn[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
     PullOffsets O;
     O.init(I.L, x, y, z);
     float fr[Q], fp[Q], g[Q7];
     pull_compact<T>(S.ns, I.P, fin, gidx + (BATCH ? I.gidx_off : 0), O, t, fr, fp, g);
-    const float delta = collide_node(I.P, lk, fr, fp, g, nme, H);
+    const float delta = collide_node<LEAN>(I.P, lk, fr, fp, g, nme, H);
     const unsigned ns = (unsigned)S.ns;
     const uint32_t seed = node_seed(fr[Q - 1], t);   // FP16 rounding bits (unused for FP32)
 #pragma unroll

@@ -553,22 +553,36 @@ __global__ void k_normal_solid(Lattice L, const uint32_t *__restrict__ list, lon
 
 // a6: H = -sum_ab (delta_ab - n_a n_b) d_a n_b, d_a n_b by Eq. finite_difference_scheme;
 // nb(i) returns the normal at x + c_i
-// (the 18 neighbours taken as 9 opposite pairs: c_opp = -c, so each pair adds
-// 3 w c_a (n_b(x + c) - n_b(x - c)), one difference per component instead of a
-// second product per nonzero c_a)
-template <class NbNormal>
+// LEAN (the FP16-storage main kernel): the 18 neighbours as 9 opposite pairs,
+// c_opp = -c, each pair adding 3 w c_a (n_b(x + c) - n_b(x - c)): one difference per
+// component instead of a second product per nonzero c_a.  The FP32 kernel keeps the
+// direction-by-direction sum, which holds fewer values at a time: at its 64-register
+// budget the pair form spills and is 3 us slower on the 128x128x256 column, while
+// the FP16 kernel gains.
+template <bool LEAN = false, class NbNormal>
 __device__ __forceinline__ float curvature(const float4 nme, const NbNormal &nb) {
   float d[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  constexpr int PAIR[9] = {0, 2, 4, 6, 7, 8, 9, 14, 15};   // i < OPP[i]
+  if constexpr (LEAN) {
+    constexpr int PAIR[9] = {0, 2, 4, 6, 7, 8, 9, 14, 15};   // i < OPP[i]
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int i = PAIR[k];
-    const float4 a = nb(i), b = nb(OPP[i]);
-    const float vx = a.x - b.x, vy = a.y - b.y, vz = a.z - b.z;
-    const float w3 = 3.0f * W[i];
-    if (CX[i]) { d[0][0] += w3 * CX[i] * vx; d[0][1] += w3 * CX[i] * vy; d[0][2] += w3 * CX[i] * vz; }
-    if (CY[i]) { d[1][0] += w3 * CY[i] * vx; d[1][1] += w3 * CY[i] * vy; d[1][2] += w3 * CY[i] * vz; }
-    if (CZ[i]) { d[2][0] += w3 * CZ[i] * vx; d[2][1] += w3 * CZ[i] * vy; d[2][2] += w3 * CZ[i] * vz; }
+    for (int k = 0; k < 9; ++k) {
+      const int i = PAIR[k];
+      const float4 a = nb(i), b = nb(OPP[i]);
+      const float vx = a.x - b.x, vy = a.y - b.y, vz = a.z - b.z;
+      const float w3 = 3.0f * W[i];
+      if (CX[i]) { d[0][0] += w3 * CX[i] * vx; d[0][1] += w3 * CX[i] * vy; d[0][2] += w3 * CX[i] * vz; }
+      if (CY[i]) { d[1][0] += w3 * CY[i] * vx; d[1][1] += w3 * CY[i] * vy; d[1][2] += w3 * CY[i] * vz; }
+      if (CZ[i]) { d[2][0] += w3 * CZ[i] * vx; d[2][1] += w3 * CZ[i] * vy; d[2][2] += w3 * CZ[i] * vz; }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q - 1; ++i) {
+      const float4 v = nb(i);
+      const float w3 = 3.0f * W[i];
+      if (CX[i]) { d[0][0] += w3 * CX[i] * v.x; d[0][1] += w3 * CX[i] * v.y; d[0][2] += w3 * CX[i] * v.z; }
+      if (CY[i]) { d[1][0] += w3 * CY[i] * v.x; d[1][1] += w3 * CY[i] * v.y; d[1][2] += w3 * CY[i] * v.z; }
+      if (CZ[i]) { d[2][0] += w3 * CZ[i] * v.x; d[2][1] += w3 * CZ[i] * v.y; d[2][2] += w3 * CZ[i] * v.z; }
+    }
   }
   const float n3[3] = {nme.x, nme.y, nme.z};
   float proj = d[0][0] + d[1][1] + d[2][2];
@@ -582,6 +596,8 @@ __device__ __forceinline__ float curvature(const float4 nme, const NbNormal &nb)
 // a2, a7 - a10 at one fluid node.  In: fr, fp, g = pulled f^r, f^p, g (g only in
 // reaction mode 0), nme = (n, |grad rho^N|), H.  Out: fr, fp, g = post-collision
 // f^r*, f^p*, g*.  Returns the reaction amount delta.
+// LEAN selects the recolouring loop's form (see below); both compute the same values.
+template <bool LEAN = false>
 __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, float (&fr)[Q], float (&fp)[Q],
                                               float (&g)[Q7], const float4 nme, float H) {
   // a2: moments
@@ -637,10 +653,29 @@ __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, 
   // the FP32-rounded weights sum to 1 + 2.5e-8, which would otherwise add that
   // much mass per node and step.
   const float Brec = P.beta * rr * rp * inv_rho;
-  // Node-level factors first, so that each direction costs a few operations:
+  if constexpr (!LEAN) {
+    float msum = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float fm_star;
+      if (i < Q - 1) {
+        fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
+        msum += fm_star;
+      } else {
+        fm_star = rho - msum;
+      }
+      const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
+      const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
+      fr[i] = r_star;
+      fp[i] = fm_star - r_star;
+    }
+  } else {
+  // LEAN: node-level factors first, so that each direction costs a few operations:
   // f^eq_i = w_i rho (A + c.u (3 + 4.5 c.u)), A = 1 - 1.5 u.u, and the recolouring
   // and reaction term w_i (Brec cos(phi_i) - delta) = +-b_a +- b_b - w_i delta with
   // b = w_i Brec n / |c_i| for the axis (|c| = 1) and diagonal (|c| = sqrt 2) classes.
+  // Fewer instructions, more values live across the loop: faster in the FP16 main
+  // kernel, 3 us slower (register spills) in the FP32 one.
   const float A = 1.0f - 1.5f * vv;
   const float wr1 = W1 * rho, wr2 = W2 * rho;
   const float b1 = W1 * Brec, b2 = W2 * Brec * RSQRT2;
@@ -664,6 +699,7 @@ __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, 
     const float r_star = fmaf(psi, fm_star, -W0 * delta);
     fr[Q - 1] = r_star;
     fp[Q - 1] = fm_star - r_star;
+  }
   }
   if (P.reaction_mode == 0) {
     // D3Q7 BGK of C advected by the physical velocity u + du/2, minus the reacted amount

@@ -296,9 +296,9 @@ __global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const __grid_consta
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) {
     const float v = 3.0f * W[i] * rn[St.nb(CX[i], CY[i], CZ[i])];
-    gx += CX[i] * v;
-    gy += CY[i] * v;
-    gz += CZ[i] * v;
+    if (CX[i]) gx += CX[i] * v;   // zero components skipped: 0 * v does not fold away
+    if (CY[i]) gy += CY[i] * v;
+    if (CZ[i]) gz += CZ[i] * v;
   }
   const int noff = BATCH ? I.node_off : 0;
   nrm[noff + node] = wetted_normal(I.P, link[noff + node], ns + noff, node, gx, gy, gz);

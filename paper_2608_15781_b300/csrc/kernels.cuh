@@ -659,12 +659,13 @@ __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, 
     for (int i = 0; i < Q; ++i) {
       float fm_star;
       if (i < Q - 1) {
-        fm_star = feq19(i, rho, vx, vy, vz, vv) + bt[i];
+        const float cu = cdot(i, vx, vy, vz);
+        fm_star = W[i] * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * vv) + bt[i];
         msum += fm_star;
       } else {
         fm_star = rho - msum;
       }
-      const float cn = (CX[i] * nme.x + CY[i] * nme.y + CZ[i] * nme.z) * INVNORM[i];
+      const float cn = cdot(i, nme.x, nme.y, nme.z) * INVNORM[i];
       const float r_star = psi * fm_star + W[i] * (Brec * cn - delta);
       fr[i] = r_star;
       fp[i] = fm_star - r_star;

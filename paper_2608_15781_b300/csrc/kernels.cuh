@@ -471,8 +471,7 @@ __device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk
       const float tx = nx_ - c * s.x, ty = ny_ - c * s.y, tz = nz_ - c * s.z;
       const float st2 = tx * tx + ty * ty + tz * tz;              // sin^2(theta')
       if (st2 >= SIN2_EPS) {
-        const float st = sqrtf(st2);
-        const float a_s = sin_th * c / st, a_n = sin_th / st;
+        const float a_n = sin_th / sqrtf(st2), a_s = a_n * c;
         const float px = (cos_th - a_s) * s.x + a_n * nx_;
         const float py = (cos_th - a_s) * s.y + a_n * ny_;
         const float pz = (cos_th - a_s) * s.z + a_n * nz_;

@@ -670,36 +670,36 @@ __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, 
       fp[i] = fm_star - r_star;
     }
   } else {
-  // LEAN: node-level factors first, so that each direction costs a few operations:
-  // f^eq_i = w_i rho (A + c.u (3 + 4.5 c.u)), A = 1 - 1.5 u.u, and the recolouring
-  // and reaction term w_i (Brec cos(phi_i) - delta) = +-b_a +- b_b - w_i delta with
-  // b = w_i Brec n / |c_i| for the axis (|c| = 1) and diagonal (|c| = sqrt 2) classes.
-  // Fewer instructions, more values live across the loop: faster in the FP16 main
-  // kernel, 3 us slower (register spills) in the FP32 one.
-  const float A = 1.0f - 1.5f * vv;
-  const float wr1 = W1 * rho, wr2 = W2 * rho;
-  const float b1 = W1 * Brec, b2 = W2 * Brec * RSQRT2;
-  const float b1x = b1 * nme.x, b1y = b1 * nme.y, b1z = b1 * nme.z;
-  const float b2x = b2 * nme.x, b2y = b2 * nme.y, b2z = b2 * nme.z;
-  const float d1 = W1 * delta, d2 = W2 * delta;
-  float msum = 0.f;
+    // LEAN: node-level factors first, so that each direction costs a few operations:
+    // f^eq_i = w_i rho (A + c.u (3 + 4.5 c.u)), A = 1 - 1.5 u.u, and the recolouring
+    // and reaction term w_i (Brec cos(phi_i) - delta) = +-b_a +- b_b - w_i delta with
+    // b = w_i Brec n / |c_i| for the axis (|c| = 1) and diagonal (|c| = sqrt 2) classes.
+    // Fewer instructions, more values live across the loop: faster in the FP16 main
+    // kernel, 3 us slower (register spills) in the FP32 one.
+    const float A = 1.0f - 1.5f * vv;
+    const float wr1 = W1 * rho, wr2 = W2 * rho;
+    const float b1 = W1 * Brec, b2 = W2 * Brec * RSQRT2;
+    const float b1x = b1 * nme.x, b1y = b1 * nme.y, b1z = b1 * nme.z;
+    const float b2x = b2 * nme.x, b2y = b2 * nme.y, b2z = b2 * nme.z;
+    const float d1 = W1 * delta, d2 = W2 * delta;
+    float msum = 0.f;
 #pragma unroll
-  for (int i = 0; i < Q - 1; ++i) {
-    const bool axis = i < 6;
-    const float cu = cdot(i, vx, vy, vz);
-    const float fm_star = (axis ? wr1 : wr2) * fmaf(cu, fmaf(4.5f, cu, 3.0f), A) + bt[i];
-    msum += fm_star;
-    const float rec = axis ? cdot(i, b1x, b1y, b1z) - d1 : cdot(i, b2x, b2y, b2z) - d2;
-    const float r_star = fmaf(psi, fm_star, rec);
-    fr[i] = r_star;
-    fp[i] = fm_star - r_star;
-  }
-  {
-    const float fm_star = rho - msum;   // rest population: cos(phi) = 0
-    const float r_star = fmaf(psi, fm_star, -W0 * delta);
-    fr[Q - 1] = r_star;
-    fp[Q - 1] = fm_star - r_star;
-  }
+    for (int i = 0; i < Q - 1; ++i) {
+      const bool axis = i < 6;
+      const float cu = cdot(i, vx, vy, vz);
+      const float fm_star = (axis ? wr1 : wr2) * fmaf(cu, fmaf(4.5f, cu, 3.0f), A) + bt[i];
+      msum += fm_star;
+      const float rec = axis ? cdot(i, b1x, b1y, b1z) - d1 : cdot(i, b2x, b2y, b2z) - d2;
+      const float r_star = fmaf(psi, fm_star, rec);
+      fr[i] = r_star;
+      fp[i] = fm_star - r_star;
+    }
+    {
+      const float fm_star = rho - msum;   // rest population: cos(phi) = 0
+      const float r_star = fmaf(psi, fm_star, -W0 * delta);
+      fr[Q - 1] = r_star;
+      fp[Q - 1] = fm_star - r_star;
+    }
   }
   if (P.reaction_mode == 0) {
     // D3Q7 BGK of C advected by the physical velocity u + du/2, minus the reacted amount
@@ -707,7 +707,7 @@ __device__ __forceinline__ float collide_node(const StepParams &P, uint32_t lk, 
 #pragma unroll
     for (int j = 0; j < Q7; ++j) {
       const int dd = GDIR[j];
-      const float geq = W7[j] * conc * (1.0f + 4.0f * (CX[dd] * wx + CY[dd] * wy + CZ[dd] * wz));
+      const float geq = W7[j] * conc * (1.0f + 4.0f * cdot(dd, wx, wy, wz));
       g[j] = g[j] + (geq - g[j]) * P.inv_tau_g - W7[j] * delta;
     }
   }

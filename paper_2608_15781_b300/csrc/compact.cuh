@@ -96,13 +96,17 @@ __device__ __forceinline__ __half half_stochastic(float x, unsigned idx) {
 
 // The main kernel stores 45 values per node: it hashes once per node (node_seed)
 // and gives population p the top 13 bits of seed * K_p, K_p an odd constant per
-// population -- one multiply per store instead of a hash per store.
+// population -- one multiply per store instead of a hash per store.  v is the
+// node's post-collision rest population, a function of every pulled value
+// (through rho and C), so it is non-finite whenever any stored value is: the seed
+// is then 0 and no random bits are added, which keeps a NaN a NaN (added to a NaN
+// pattern such as 0x7fffffff they would carry into the sign bit).
 __device__ __forceinline__ uint32_t node_seed(float v, unsigned t) {
   uint32_t h = (__float_as_uint(v) ^ (t * 0x85EBCA6Bu)) * 0x9E3779B9u;
   h ^= h >> 15;
   h *= 0x2C1B3C6Du;
   h ^= h >> 13;
-  return h * 0x27D4EB2Fu;
+  return isfinite(v) ? h * 0x27D4EB2Fu : 0u;
 }
 __device__ __forceinline__ uint32_t pop_random(uint32_t seed, int p) {
   return seed * ((0x9E3779B9u ^ ((uint32_t)p * 0x632BE5ABu)) | 1u);
@@ -116,11 +120,10 @@ struct Store<__half> {
   static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned idx, int p, float v) {
     f[idx] = half_stochastic(v - pop_ref(p), idx);
   }
-  // the same rounding with the random word r supplied by the caller (top 13 bits used)
+  // the same rounding with the random word r supplied by the caller (top 13 bits
+  // used); the caller passes r = 0 for a node with a non-finite value (node_seed)
   static __device__ __forceinline__ void st_r(__half *__restrict__ f, unsigned idx, int p, float v, uint32_t r) {
-    const uint32_t bits = __float_as_uint(v - pop_ref(p));
-    const uint32_t add = (bits & 0x7f800000u) == 0x7f800000u ? 0u : (r >> 19);
-    f[idx] = __float2half_rz(__uint_as_float(bits + add));
+    f[idx] = __float2half_rz(__uint_as_float(__float_as_uint(v - pop_ref(p)) + (r >> 19)));
   }
 };
 
@@ -444,7 +447,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     pull_compact<T>(S.ns, I.P, fin, gidx + (BATCH ? I.gidx_off : 0), O, t, fr, fp, g);
     const float delta = collide_node<LEAN>(I.P, lk, fr, fp, g, nme, H);
     const unsigned ns = (unsigned)S.ns;
-    const uint32_t seed = node_seed(fr[Q - 1], t);   // FP16 rounding bits (unused for FP32)
+    // FP16 rounding bits (unused for FP32); fr + fp of the rest population sums rho
+    // and, in reaction mode 0, g[6] carries C: both enter the finiteness check
+    const uint32_t seed = node_seed(fr[Q - 1] + fp[Q - 1] + (I.P.reaction_mode == 0 ? g[Q7 - 1] : 0.f), t);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       Store<T>::st_r(fout, (unsigned)i * ns + t, i, fr[i], pop_random(seed, i));

@@ -110,6 +110,14 @@ def test_fp16_stochastic_rounding_is_unbiased_and_reproducible():
         L.set_state(g)
         assert np.isnan(L.get_state()[4, 0, 0, 2])
         assert L.observables(allow_nan=True)["n_bad"] >= 1
+        L.step(1)                                # ... also after the main kernel's FP16 stores
+        assert np.isnan(L.get_state()).any()
+        assert L.observables(allow_nan=True)["n_bad"] >= 1
+        g = f.copy()
+        g[40, 1, 1, 1] = np.nan                  # a NaN in the reactant populations (g) as well
+        L.set_state(g)
+        L.step(1)
+        assert L.observables(allow_nan=True)["n_bad"] >= 1
     assert np.array_equal(a, b)
     dev = a[1].astype(np.float64) - W19[1] - 2.0 ** -7
     up = np.isclose(dev, h, atol=h / 8)

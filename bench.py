@@ -347,6 +347,7 @@ def run_native(args):
         barrier()
         t0 = time.perf_counter()
         L2 = lbm.Lattice(solid_h, head, bc_z=wl.bc_z, stream=stream.cuda_stream)
+        t_create = time.perf_counter() - t0
         for k in range(args.steps):
             L2.step(1)
             L2.reaction_async(base + 16 * k)
@@ -360,6 +361,7 @@ def run_native(args):
         d2h = 16 * args.steps + 4 * N + 8 * 8 * 2    # reaction sums per step, link readback, observables
         e2e = {"value": round(whole_job_mlups(world, N, args.steps, te * 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": round(h2d / args.steps, 2), "d2h_bytes_per_step": round(d2h / args.steps, 2),
+               "create_ms": round(t_create * 1e3, 1),
                "includes": "lbm_create from the host mask (geometry precompute on the GPU, slot layout on the "
                            "host), per step lbm_step(1) + lbm_reaction_async (D2H of the step's reaction sums "
                            "into pinned memory), lbm_observables (synchronises), lbm_destroy"}

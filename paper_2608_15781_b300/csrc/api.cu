@@ -6,11 +6,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <memory>
 #include <new>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -523,6 +526,28 @@ int fill_obs(Batch &b, lbm_obs *out, int count) {
 
 // Build a batch: validate, precompute every instance's geometry on the GPU,
 // lay out the slot space, start from equilibrium.
+// f(c) for every c in [0, nchunks), spread over up to 32 host threads (the caller
+// included); if no thread can be started the caller does all of them
+template <class F>
+void parallel_chunks(int nchunks, F &&f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = std::min(nchunks, (int)std::min(32u, std::max(1u, hw)));
+  std::atomic<int> next{0};
+  auto work = [&] {
+    for (int c = next.fetch_add(1); c < nchunks; c = next.fetch_add(1)) f(c);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {
+      break;
+    }
+  }
+  work();
+  for (std::thread &th : pool) th.join();
+}
+
 int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *params, void *stream) {
   if (n < 1 || n > 65535 || !geoms || !params) return LBM_EINVAL;
   for (int k = 0; k < n; ++k) {
@@ -603,67 +628,117 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
     if (rc) return cuda_fail(b, cudaErrorUnknown);
     CK(cudaMemcpy(hlink.data(), b.link, nodes * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   }
-  // slot space: per instance its fluid slots in lattice order, then its ghost planes
-  std::vector<uint32_t> hnode, hbnd;
-  std::vector<uint16_t> hkid, hbkid;
-  std::vector<int> hgidx((size_t)gtot, -1);
-  {
-    long long ghost_slots = 0;
-    for (int k = 0; k < n; ++k) ghost_slots += b.h[k].d.L.bc_z == 1 ? 2 * b.h[k].d.L.plane : 0;
-    hnode.reserve((size_t)(nodes + ghost_slots));
-    if (n > 1) hkid.reserve((size_t)(nodes + ghost_slots));
+  // slot space: per instance its fluid slots in lattice order, then its ghost planes.
+  // Built plane-parallel in two passes (counts per plane, then direct fills at the
+  // prefix-summed offsets): the same layout as one sequential pass over the nodes.
+  struct PlaneCount {
+    long long fluid = 0, bnd = 0, wall = 0;
+  };
+  std::vector<std::vector<PlaneCount>> cnt(n);
+  for (int k = 0; k < n; ++k) {
+    const Lattice &L = b.h[k].d.L;
+    const uint32_t *lk = hlink.data() + b.h[k].d.node_off;
+    std::vector<PlaneCount> &c = cnt[k];
+    c.resize((size_t)L.nz);
+    parallel_chunks(L.nz, [&](int z) {
+      const uint32_t *w = lk + (long long)z * L.plane;
+      PlaneCount pc;
+      for (long long q = 0; q < L.plane; ++q) {
+        const uint32_t v = w[q];
+        if (v & BIT_SOLID) {
+          pc.bnd += (v & BIT_SOLID_BND) ? 1 : 0;
+        } else {
+          pc.fluid += 1;
+          pc.wall += (v & BIT_WALL) ? 1 : 0;
+        }
+      }
+      c[(size_t)z] = pc;
+    });
   }
-  long long s = 0;
+  long long s = 0, nbnd_tot = 0;
+  std::vector<long long> slot0(n), bnd0(n);
+  for (int k = 0; k < n; ++k) {
+    InstHost &ih = b.h[k];
+    const Lattice &L = ih.d.L;
+    slot0[k] = s;
+    bnd0[k] = nbnd_tot;
+    long long nf = 0;
+    for (const PlaneCount &pc : cnt[k]) {
+      nf += pc.fluid;
+      ih.n_bnd += pc.bnd;
+      ih.n_wall += pc.wall;
+    }
+    if (nf == 0) return LBM_EINVAL;
+    ih.d.slot_off = (int)s;
+    ih.d.nf = (int)nf;
+    ih.n_fluid = nf;
+    ih.d.ghost = (int)(s + nf);
+    s += nf + (L.bc_z == 1 ? 2 * L.plane : 0);
+    nbnd_tot += ih.n_bnd;
+    if (s > (1ll << 31) - 1) return LBM_EINVAL;
+  }
+  std::vector<uint32_t> hnode((size_t)s), hbnd((size_t)nbnd_tot);
+  std::vector<uint16_t> hkid(n > 1 ? (size_t)s : 0), hbkid(n > 1 ? (size_t)nbnd_tot : 0);
+  std::unique_ptr<int[]> hgidx_buf(new (std::nothrow) int[(size_t)std::max(gtot, 1ll)]);
+  if (!hgidx_buf) return LBM_ENOMEM;
+  int *const hgidx = hgidx_buf.get();
   for (int k = 0; k < n; ++k) {
     InstHost &ih = b.h[k];
     const Lattice &L = ih.d.L;
     const uint32_t *lk = hlink.data() + ih.d.node_off;
-    int *gi = hgidx.data() + ih.d.gidx_off + L.plane;   // gi[node index], planes -1 and nz outside
-    ih.d.slot_off = (int)s;
-    ih.slot_node.reserve((size_t)L.n);
-    long long i = 0;
-    for (uint32_t z = 0; z < (uint32_t)L.nz; ++z)
+    int *gi = hgidx + ih.d.gidx_off + L.plane;   // gi[node index], planes -1 and nz outside
+    ih.slot_node.resize((size_t)ih.d.nf);
+    const std::vector<PlaneCount> &c = cnt[k];
+    std::vector<long long> f0((size_t)L.nz), b0((size_t)L.nz);
+    long long fa = 0, ba = 0;
+    for (int z = 0; z < L.nz; ++z) {
+      f0[(size_t)z] = fa;
+      b0[(size_t)z] = ba;
+      fa += c[(size_t)z].fluid;
+      ba += c[(size_t)z].bnd;
+    }
+    const uint16_t kk = (uint16_t)k;
+    parallel_chunks(L.nz, [&](int z) {
+      long long fl = f0[(size_t)z], bl = bnd0[k] + b0[(size_t)z];
+      long long i = (long long)z * L.plane;
       for (uint32_t y = 0; y < (uint32_t)L.ny; ++y)
         for (uint32_t x = 0; x < (uint32_t)L.nx; ++x, ++i) {
           const uint32_t w = lk[i];
-          const uint32_t pk = x | (y << 10) | (z << 20);
+          const uint32_t pk = x | (y << 10) | ((uint32_t)z << 20);
           if (w & BIT_SOLID) {
+            gi[i] = -1;
             if (w & BIT_SOLID_BND) {
-              hbnd.push_back(pk);
-              if (n > 1) hbkid.push_back((uint16_t)k);
-              ih.n_bnd++;
+              hbnd[(size_t)bl] = pk;
+              if (n > 1) hbkid[(size_t)bl] = kk;
+              ++bl;
             }
             continue;
           }
-          if (w & BIT_WALL) ih.n_wall++;
-          gi[i] = (int)s;
-          ih.slot_node.push_back((uint32_t)i);
-          hnode.push_back(pk);
-          if (n > 1) hkid.push_back((uint16_t)k);
-          ++s;
+          const long long sl = slot0[k] + fl;
+          gi[i] = (int)sl;
+          ih.slot_node[(size_t)fl] = (uint32_t)i;
+          hnode[(size_t)sl] = pk;
+          if (n > 1) hkid[(size_t)sl] = kk;
+          ++fl;
         }
-    ih.d.nf = (int)(s - ih.d.slot_off);
-    ih.n_fluid = ih.d.nf;
-    if (ih.n_fluid == 0) return LBM_EINVAL;
-    ih.d.ghost = (int)s;
-    if (L.bc_z == 1) {
-      for (long long q = 0; q < L.plane; ++q) {
-        gi[q - L.plane] = (int)(s + q);                         // inlet plane z = -1
-        gi[L.nz * L.plane + q] = (int)(s + L.plane + q);        // outlet plane z = nz
-      }
-      for (long long q = 0; q < 2 * L.plane; ++q) {
-        hnode.push_back(kNoNode);
-        if (n > 1) hkid.push_back((uint16_t)k);
-      }
-      s += 2 * L.plane;
+    });
+    const long long g = ih.d.ghost;
+    for (long long q = 0; q < L.plane; ++q) {
+      gi[q - L.plane] = L.bc_z == 1 ? (int)(g + q) : -1;                     // inlet plane z = -1
+      gi[L.nz * L.plane + q] = L.bc_z == 1 ? (int)(g + L.plane + q) : -1;    // outlet plane z = nz
     }
-    if (s > (1ll << 31) - 1) return LBM_EINVAL;
+    if (L.bc_z == 1) {
+      for (long long q = 0; q < 2 * L.plane; ++q) {
+        hnode[(size_t)(g + q)] = kNoNode;
+        if (n > 1) hkid[(size_t)(g + q)] = kk;
+      }
+    }
   }
   b.nslots = (int)s;
   // every slot-map entry is a slot of the space or -1 (solid): the kernels index
   // population arrays with these values
-  for (int v : hgidx)
-    if (v < -1 || v >= b.nslots) return LBM_EINVAL;
+  for (long long q = 0; q < gtot; ++q)
+    if (hgidx[q] < -1 || hgidx[q] >= b.nslots) return LBM_EINVAL;
   b.ns = (int)((s + 63) / 64 * 64);
   if ((long long)NPOP * b.ns >= (1ll << 32)) return LBM_EINVAL;   // 32-bit population offsets
   b.n_bnd = (int)hbnd.size();
@@ -683,7 +758,7 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   for (int k = 0; k < n; ++k) hinst[k] = b.h[k].d;
   CK(cudaMemsetAsync(b.buf0, 0, pop_bytes, b.stream));
   CK(cudaMemsetAsync(b.buf1, 0, pop_bytes, b.stream));
-  CK(cudaMemcpy(b.gidx, hgidx.data(), hgidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b.gidx, hgidx, (size_t)gtot * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(b.node, hnode.data(), hnode.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(b.inst, hinst.data(), n * sizeof(Inst), cudaMemcpyHostToDevice));
   if (b.kid) CK(cudaMemcpy(b.kid, hkid.data(), hkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));

@@ -450,6 +450,9 @@ def cm_collision_backtransform(fm, u, tau, chunk=65536):
     relax[5:10] = 1.0 / tau
     one_minus_R = 1.0 - relax
     N = fm.shape[1]
+    if not one_minus_R.any():
+        # tau = 1: R = I, so k* = 0 and the solution of T y = 0 is y = 0
+        return np.zeros((Q19, N), dtype=dt)
     out = np.empty((Q19, N), dtype=dt)
     for s in range(0, N, chunk):
         e = min(N, s + chunk)

@@ -7,13 +7,13 @@ Two kinds of check:
   step to FP32 rounding: populations to 5e-7 absolute (they are O(0.1)).
   Integer-valued fields (NN) must agree exactly.
 * Trajectory parity.  Over hundreds of steps the two-phase dynamics amplify
-  rounding differences at a few sensitive spots (continuing the FP64 oracle
-  from the GPU's step-50 state reproduces the GPU's step-200 difference
-  exactly, so the amplification is the method's, not the kernel's).  Bounds:
-  observables (FP64 reductions) to 2e-5 relative, field percentiles p50 /
-  p99 / max of rho^r to 1e-5 / 2e-3 / 1e-2 -- about 4x what the FP32
-  instantiation of the oracle itself shows (3e-6 / 7e-5 / 3.6e-4) for p50 and
-  4x the observed GPU spread for the tail.
+  rounding differences at a few sensitive spots, so the GPU's distance from
+  the FP64 oracle is bounded by the oracle's own FP32 rounding spread: the
+  oracle is run in FP32 three times (from the FP32-rounded start and from two
+  starts moved by one ulp per population), and per percentile (p50, p99, max
+  over the fluid nodes) |GPU - FP64| must stay within 4x the largest
+  |FP32 oracle - FP64| of those draws, plus a floor of a few FP32 spacings.
+  Observables (FP64 reductions) to 2e-5 relative.
 """
 import math
 
@@ -27,11 +27,9 @@ from paper_2608_15781_b300 import build, lbm, synth
 pytestmark = pytest.mark.gpu
 
 TOL_STEP_POP = 5e-7          # one step from a given state, populations, max-abs
-TOL_RHO_P50 = 1e-5           # trajectory, rho^r / rho^p, median over fluid nodes
-TOL_RHO_P99 = 2e-3
-TOL_RHO_MAX = 1e-2
-TOL_C_MAX = 5e-4
-TOL_U_MAX = 1e-4
+TRAJ_FACTOR = 4.0            # trajectory: multiple of the oracle's own FP32 spread
+TRAJ_FLOOR = {"rho_r": 2e-6, "rho_p": 2e-6, "C": 2e-6, "u": 2e-7}   # a few FP32 spacings
+TRAJ_PCT = (50, 99, 100)
 TOL_MASS_REL = 2e-5
 
 
@@ -82,12 +80,13 @@ def test_geometry_fields(bc):
 # --------------------------------------------------------------------- one step
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("nx", [37, 36])
+@pytest.mark.parametrize("nx", [37, 32])
 def test_single_step_random_state(bc, mode, nx):
-    """Ragged box, random mask and non-equilibrium state.
+    """Random mask and non-equilibrium state on a box of odd and of warp-multiple width.
 
-    nx = 37 runs the one-thread-per-node main kernel, nx = 36 the row-staged one
-    (rows of 36 floats staged by bulk copies; y = 21 is not a multiple of the block).
+    In both the fluid-slot count is not a multiple of any launch block, so every
+    kernel runs a partial last block; the odd width also wraps x periodically at
+    a non-aligned row end.
     """
     shape = (19, 21, nx)
     rng = np.random.default_rng(100 + bc + 2 * mode)
@@ -184,15 +183,45 @@ def _check_checkpoints(cps, g, op):
         assert err < TOL_STEP_POP, (k, err)
 
 
-def _check_trajectory(out, ref, fl):
-    a, b = _moments(out), _moments(ref)
-    for comp in (0, 1):
-        d = np.abs(a[comp] - b[comp])[fl]
-        assert np.median(d) < TOL_RHO_P50, (comp, np.median(d))
-        assert np.percentile(d, 99) < TOL_RHO_P99, (comp, np.percentile(d, 99))
-        assert d.max() < TOL_RHO_MAX, (comp, d.max())
-    assert np.abs(a[2] - b[2])[fl].max() < TOL_C_MAX
-    assert np.abs(a[3] - b[3])[:, fl].max() < TOL_U_MAX
+def _fp32_draws(st0, g, op, nsteps, draws=3, seed=0):
+    """Final states of the oracle run in FP32 from the FP32-rounded start and from starts moved
+    by one ulp per population (random direction): samples of what FP32 rounding alone does."""
+    rng = np.random.default_rng(seed)
+    f0 = st0.f.astype(np.float32)
+    out = []
+    for k in range(draws):
+        f = f0.copy()
+        if k:
+            away = np.where(rng.random(f.shape) < 0.5, np.float32(np.inf), np.float32(-np.inf))
+            f = np.nextafter(f, away).astype(np.float32)
+            f[:, g.solid] = 0.0
+        st = O.State(f=f, mc0=st0.mc0)
+        out.append(O.run(st, g, op, nsteps).f)
+    return out
+
+
+def _trajectory_dists(f, ref, fl):
+    a, b = _moments(f), _moments(ref)
+    return {"rho_r": np.abs(a[0] - b[0])[fl], "rho_p": np.abs(a[1] - b[1])[fl], "C": np.abs(a[2] - b[2])[fl],
+            "u": np.abs(a[3] - b[3])[:, fl].max(axis=0)}
+
+
+def _check_trajectory(out, ref, fl, draws32):
+    """|GPU - FP64| per percentile within TRAJ_FACTOR x the largest FP32-oracle spread + floor.
+
+    Returns {quantity: [(percentile, gpu, fp32 spread)]} for reporting."""
+    dg = _trajectory_dists(out, ref, fl)
+    d32 = [_trajectory_dists(f, ref, fl) for f in draws32]
+    report = {}
+    for k, d in dg.items():
+        rows = []
+        for q in TRAJ_PCT:
+            spread = max(float(np.percentile(x[k], q)) for x in d32)
+            got = float(np.percentile(d, q))
+            rows.append((q, got, spread))
+            assert got <= TRAJ_FACTOR * spread + TRAJ_FLOOR[k], (k, q, got, spread)
+        report[k] = rows
+    return report
 
 
 def test_c1_periodic_200_steps():
@@ -208,9 +237,10 @@ def test_c1_periodic_200_steps():
         out = L.get_state()
         ob = L.observables()
     _check_checkpoints(cps, g, op)
-    st = O.run(O.init_state(g, op), g, op, 200)
+    st0 = O.init_state(g, op)
+    st = O.run(st0, g, op, 200)
     oo = O.observables(st, g, op)
-    _check_trajectory(out, st.f, g.fluid)
+    print("trajectory c1 periodic 200 steps", _check_trajectory(out, st.f, g.fluid, _fp32_draws(st0, g, op, 200)))
     for k in ("mass_r", "mass_p", "mass_c", "consumed"):
         assert abs(ob[k] - oo[k]) < TOL_MASS_REL * abs(oo["mass_r"] + oo["mass_p"]), k
     assert abs(ob["gas_saturation"] - oo["gas_saturation"]) < 1e-5
@@ -229,9 +259,10 @@ def test_column_inlet_outlet_100_steps():
         out = L.get_state()
         ob = L.observables()
     _check_checkpoints(cps, g, op)
-    st = O.run(O.init_state(g, op), g, op, 100)
+    st0 = O.init_state(g, op)
+    st = O.run(st0, g, op, 100)
     oo = O.observables(st, g, op)
-    _check_trajectory(out, st.f, g.fluid)
+    print("trajectory column 100 steps", _check_trajectory(out, st.f, g.fluid, _fp32_draws(st0, g, op, 100)))
     for k in ("flux_in", "flux_out"):
         assert abs(ob[k] - oo[k]) < 5e-4 * abs(oo["flux_in"]), k
     assert abs(ob["conversion"] - oo["conversion"]) < 5e-4
@@ -256,10 +287,10 @@ def test_droplets_paper_mode_nucleation_sites():
         out = L.get_state()
         ob = L.observables()
     _check_checkpoints(cps, g, op)
-    st = O.init_state(g, op, rho_r=rr.astype(np.float32), rho_p=rp.astype(np.float32))
-    st = O.run(st, g, op, 100)
+    st0 = O.init_state(g, op, rho_r=rr.astype(np.float32), rho_p=rp.astype(np.float32))
+    st = O.run(st0, g, op, 100)
     oo = O.observables(st, g, op)
-    _check_trajectory(out, st.f, g.fluid)
+    print("trajectory droplets paper mode 100 steps", _check_trajectory(out, st.f, g.fluid, _fp32_draws(st0, g, op, 100)))
     assert abs(ob["consumed"] - oo["consumed"]) < TOL_MASS_REL * oo["mass_r"]
     assert abs(ob["rate"] - oo["rate"]) < 1e-4 * max(oo["rate"], 1e-3)
 

@@ -3,7 +3,9 @@
   P1 flat interface: a planar r|p slab stays sharp, symmetric and at rest
      (recolouring of Eq. operator_recoloring with n along +grad rho^N).
   P2 Laplace law: dp = sigma / R for a cylindrical r-droplet and p-bubble, the
-     higher pressure inside both (Eq. continuum_surface_force, Eq. interface_curvature).
+     higher pressure inside both (Eq. continuum_surface_force, Eq. interface_curvature);
+     the discrete curvature of smooth spherical and cylindrical colour fields is
+     2/R and 1/R, the same along every axis.
   P4 Poiseuille: body-force channel flow between halfway bounce-back walls; the
      bulk second difference of u_x is -a/nu with nu = c_s^2 (tau - 1/2)
      (Eq. kinematic_viscosity) and the centre-line value is a H^2 / (8 nu).
@@ -88,6 +90,39 @@ def _laplace(R0, inverse, n=40, sigma=0.02, steps=900):
     R = math.sqrt(inner / math.pi)
     dp = (rho[r < R - 4].mean() - rho[r > R + 4].mean()) * O.CS2
     return dp, sigma / R
+
+
+def _curvature_of(phi):
+    g = O.Geometry(solid=np.zeros(phi.shape, bool), bc_z=0)
+    grad = O.gradient(phi, g)
+    gm = np.sqrt((grad * grad).sum(axis=0))
+    n = np.where(gm >= 1e-5, grad / np.where(gm > 0, gm, 1.0), 0.0)
+    return O.curvature(n, g)
+
+
+@pytest.mark.parametrize("R", [8, 12, 16])
+def test_curvature_of_spheres_and_cylinders(R):
+    """Eq. interface_curvature with the stencil of Eq. finite_difference_scheme on a smooth colour
+    field tanh((R - r)/2): H = 2/R on a sphere (within 1 %), 1/R on a cylinder along x, y or z
+    (within 2.5 %), and the three cylinders give the same values node by node (the stencil is
+    symmetric under axis permutation, so a wrong z term shows as a difference)."""
+    n = 2 * R + 12
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+    c = n / 2 - 0.5
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    H = _curvature_of(np.tanh((R - r) / 2.0))
+    shell = np.abs(r - R) < 0.5
+    assert abs(H[shell].mean() * R / 2 - 1) < 0.01
+    cyl = []
+    for a, rr in enumerate((np.sqrt((y - c) ** 2 + (z - c) ** 2), np.sqrt((x - c) ** 2 + (z - c) ** 2),
+                            np.sqrt((x - c) ** 2 + (y - c) ** 2))):
+        Hc = _curvature_of(np.tanh((R - rr) / 2.0))
+        ring = np.abs(rr - R) < 0.5
+        assert abs(Hc[ring].mean() * R - 1) < 0.025
+        cyl.append(np.moveaxis(Hc, 2 - a, 0))     # the cylinder axis first
+    # with the axis first, the remaining axes are the cross-section, symmetric in its two axes
+    for Hc in cyl[:2]:
+        assert np.abs(Hc - cyl[2]).max() < 1e-9
 
 
 @pytest.mark.parametrize("R0,inverse", [(10, False), (10, True)])

@@ -173,23 +173,31 @@ int lbm_set_debug(lbm_ctx *ctx, int32_t enable);
 
 /* Per-kernel timing with CUDA events on the context's stream.  Kernel kinds:
  * 0 density, 1 solid colour, 2 normal, 3 solid normal, 4 main step,
- * 5 observables.  lbm_profile(ctx, 1) resets and starts; lbm_profile_read
- * synchronises and returns total milliseconds and launch counts (n <= 6). */
-#define LBM_NKERNELS 6
+ * 5 observables, 6 fused fields (solid colour, normals and solid normals in
+ * one launch that marches through z with shared-memory planes, replacing
+ * kinds 1-3).  lbm_profile(ctx, 1) resets and
+ * starts; lbm_profile_read synchronises and returns total milliseconds and
+ * launch counts (n <= 7). */
+#define LBM_NKERNELS 7
 int lbm_profile(lbm_ctx *ctx, int32_t enable);
 int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
 /* Launch configuration of the step (not part of the paper): lbm_tune times each
  * candidate on the current state (main kernel 64/128/256 threads; colour-function
- * and normal kernels 128/256/512; then whole steps with the four kernels after
- * the first launched as programmatic dependent launches, which lets each one be
- * scheduled while its predecessor's last blocks run, or as plain launches) and
- * keeps the fastest; blocks[4] (may be NULL) receives the choice (main, density,
- * normal, programmatic 1 / plain 0).  Every choice gives bit-identical results.
- * The state is not advanced.  Without a call: 128, 256, 256, 1. */
+ * and normal kernels 128/256/512; then whole steps with the colour at solids,
+ * the normals and the normals at solids as three kernels or as one kernel that
+ * marches through z-chunks of 16, 32 or 64 planes with the colour field staged
+ * in shared memory; then whole steps with the
+ * kernels after the first launched as programmatic dependent launches, which
+ * lets each one be scheduled while its predecessor's last blocks run, or as
+ * plain launches) and keeps the fastest; blocks[5] (may be NULL) receives the
+ * choice (main, density, normal, programmatic 1 / plain 0, fields: 0 three
+ * kernels, 1 / 2 / 3 one marching kernel with chunks of 16 / 32 / 64 planes).
+ * Every choice gives bit-identical results.  The state is not advanced.
+ * Without a call: 128, 256, 256, 1, 0. */
 int lbm_tune(lbm_ctx *ctx, int32_t *blocks);
 
-/* Set the launch configuration directly (blocks[4] as filled by lbm_tune, e.g. a
+/* Set the launch configuration directly (blocks[5] as filled by lbm_tune, e.g. a
  * tuning saved earlier).  LBM_EINVAL for a value outside the candidates.  The next step
  * rebuilds the step's CUDA graphs. */
 int lbm_set_launch(lbm_ctx *ctx, const int32_t *blocks);
@@ -287,8 +295,12 @@ void lbm_batch_destroy(lbm_batch *batch);
  *   solid         device, nx*ny*nz bytes, nonzero = solid (layout as lbm_geometry).
  *   reactive      device, optional r(x) mask, or NULL (fluid nodes with NN >= 1).
  *   f_in, f_out   device, 45 * nx*ny*nz floats each in the lbm_get_state layout
- *                 (index p * N + node); f_out receives the post-collision
- *                 populations of the step.  They must not overlap.
+ *                 (index p * N + node); every entry of f_out is written: the
+ *                 post-collision populations of the step at fluid nodes, zero
+ *                 at solid nodes, and in the paper's reaction mode
+ *                 (reaction_mode = 1, which does not evolve the reactant) the
+ *                 seven reactant populations copied from f_in.  They must not
+ *                 overlap.
  *   delta_sum     device, one double receiving the step's sum of reaction
  *                 amounts, or NULL.
  *   params        as for lbm_create (cuda_stream selects the stream; only
@@ -303,7 +315,9 @@ void lbm_batch_destroy(lbm_batch *batch);
  * cleared at the start of each call): calls that may overlap on the GPU --
  * different streams, different host threads -- race and must be serialised by
  * the caller.  Returns LBM_OK, LBM_EINVAL or LBM_ECUDA (launch errors; kernel
- * faults surface at the caller's next synchronisation). */
+ * faults surface at the caller's next synchronisation).  A CUDA error already
+ * pending on the calling thread when the call starts is reported as
+ * LBM_ECUDA before anything is launched and is left pending for the caller. */
 #define LBM_STATIC_MAX_NODES 131072
 int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, const uint8_t *reactive,
                     const float *f_in, float *f_out, double *delta_sum, const lbm_params *params);

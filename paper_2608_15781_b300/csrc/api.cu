@@ -65,7 +65,11 @@ struct Batch {
   int sticky = LBM_OK;
   // launch shapes (lbm_tune picks them by timing)
   int main_block = 128, dens_block = 256, norm_block = 256;
-  bool pdl = true;                    // programmatic dependent launch of the step's kernels 2-5
+  bool pdl = true;                    // programmatic dependent launch of the step's kernels after the first
+  int fields = 0;                     // 0: colour, normals, solid normals as three kernels; 1, 2, 3: one
+                                      // z-marching launch with chunks of kChunk[fields - 1] planes
+  int *block_off = nullptr;           // first marching block of each instance, per chunk option ((n + 1) x 3)
+  int n_blocks[3] = {0, 0, 0};        // marching blocks of all instances, per chunk option
   // CUDA graphs of one step, for even and odd steps
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graphs_valid = false;
@@ -153,7 +157,7 @@ void drop_graphs(Batch &b) {
 void free_all(Batch &b) {
   drop_graphs(b);
   void *ptrs[] = {b.inst, b.kid, b.node, b.buf0, b.buf1, b.gidx, b.link, b.nsv, b.nrm, b.rhoN, b.bnd, b.bnd_kid,
-                  b.acc, b.acc_scratch, b.obs, b.err, b.dbg_H, b.dbg_delta};
+                  b.acc, b.acc_scratch, b.obs, b.err, b.dbg_H, b.dbg_delta, b.block_off};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
   b.ev.clear();
@@ -235,16 +239,16 @@ Slots slots(const Batch &b) { return Slots{b.inst, b.kid, b.node, b.nslots, b.ns
 // with pdl, as a programmatic dependent launch (the kernel itself waits for its
 // predecessor in pdl_begin), else a plain launch.
 template <typename... KArgs, typename... Args>
-void launch_step_kernel(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
-                        Args... args) {
+void launch_step_kernel_smem(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t st, Args... args) {
   if (!pdl) {
-    k<<<grid, block, 0, st>>>(args...);
+    k<<<grid, block, smem, st>>>(args...);
     return;
   }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -252,6 +256,11 @@ void launch_step_kernel(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned b
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k, args...);
+}
+template <typename... KArgs, typename... Args>
+void launch_step_kernel(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                        Args... args) {
+  launch_step_kernel_smem(pdl, k, grid, block, 0, st, args...);
 }
 
 template <typename T, bool BT>
@@ -356,6 +365,43 @@ void launch_solids(const Batch &b, cudaStream_t st, bool colour) {
   }
 }
 
+// xy tile of the z-marching field kernel (k_fields_march) and its chunk lengths in z
+constexpr int FTX = 32, FTY = 16;
+constexpr int kChunk[3] = {16, 32, 64};
+using FTile = MarchTile<FTX, FTY>;
+
+int march_blocks(const Lattice &L, int chunk) {
+  return ((L.nx + FTX - 1) / FTX) * ((L.ny + FTY - 1) / FTY) * ((L.nz + chunk - 1) / chunk);
+}
+
+// the shared-memory opt-in of the marching field kernel, on the current device
+int fields_attributes() {
+  const int bytes = (int)FTile::smem_bytes();
+  if (cudaFuncSetAttribute(k_fields_march<FTX, FTY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_fields_march<FTX, FTY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+// a3 - a5 and the normals at solids of every instance in one launch (see k_fields_march)
+void launch_fields_march(const Batch &b, cudaStream_t st) {
+  const Inst &I = b.h[0].d;
+  const int opt = b.fields - 1, chunk = kChunk[opt];
+  const int *off = b.block_off ? b.block_off + opt * (b.n + 1) : nullptr;
+  if (b.n > 1)
+    launch_step_kernel_smem(b.pdl, k_fields_march<FTX, FTY, true>, (unsigned)b.n_blocks[opt], 256,
+                            FTile::smem_bytes(), st, (const Inst *)b.inst, I, off, b.n, chunk,
+                            (const uint32_t *)b.link, (const float4 *)b.nsv, b.rhoN, b.nrm);
+  else
+    launch_step_kernel_smem(b.pdl, k_fields_march<FTX, FTY, false>, (unsigned)b.n_blocks[opt], 256,
+                            FTile::smem_bytes(), st, (const Inst *)b.inst, I, off, b.n, chunk,
+                            (const uint32_t *)b.link, (const float4 *)b.nsv, b.rhoN, b.nrm);
+}
+
 // the kernels of one step (in -> out), on stream st
 void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int slot, bool prof,
                   double *acc = nullptr) {
@@ -366,18 +412,24 @@ void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int sl
     pb(0);
     launch_density<T>(b, st, fin);
     pe();
-    if (b.n_bnd > 0) {
-      pb(1);
-      launch_solids(b, st, true);
+    if (b.fields) {
+      pb(6);
+      launch_fields_march(b, st);
       pe();
-    }
-    pb(2);
-    launch_normal(b, st);
-    pe();
-    if (b.n_bnd > 0) {
-      pb(3);
-      launch_solids(b, st, false);
+    } else {
+      if (b.n_bnd > 0) {
+        pb(1);
+        launch_solids(b, st, true);
+        pe();
+      }
+      pb(2);
+      launch_normal(b, st);
       pe();
+      if (b.n_bnd > 0) {
+        pb(3);
+        launch_solids(b, st, false);
+        pe();
+      }
     }
     pb(4);
     launch_main<T>(b, st, fin, fout, acc ? acc : b.acc, slot);
@@ -742,6 +794,18 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   b.ns = (int)((s + 63) / 64 * 64);
   if ((long long)NPOP * b.ns >= (1ll << 32)) return LBM_EINVAL;   // 32-bit population offsets
   b.n_bnd = (int)hbnd.size();
+  // blocks of the marching field kernel, numbered instance by instance, per chunk option
+  std::vector<int> hblock(3 * (size_t)(n + 1), 0);
+  for (int o = 0; o < 3; ++o) {
+    int *hb = hblock.data() + o * (n + 1);
+    for (int k = 0; k < n; ++k) {
+      const long long nb = (long long)hb[k] + march_blocks(b.h[k].d.L, kChunk[o]);
+      if (nb > (1ll << 31) - 1) return LBM_EINVAL;
+      hb[k + 1] = (int)nb;
+    }
+    b.n_blocks[o] = hb[n];
+  }
+  if (fields_attributes() != LBM_OK) b.fields = 0;   // no shared-memory opt-in: the three kernels
   const size_t elt = b.half ? sizeof(__half) : sizeof(float);
   const size_t pop_bytes = (size_t)NPOP * b.ns * elt;
   rc = rc ? rc : dalloc(b, &b.buf0, pop_bytes);
@@ -749,6 +813,7 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   rc = rc ? rc : dalloc(b, (void **)&b.node, hnode.size() * sizeof(uint32_t));
   rc = rc ? rc : dalloc(b, (void **)&b.inst, n * sizeof(Inst));
   if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.kid, hkid.size() * sizeof(uint16_t));
+  if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.block_off, hblock.size() * sizeof(int));
   if (b.n_bnd > 0) {
     rc = rc ? rc : dalloc(b, (void **)&b.bnd, hbnd.size() * sizeof(uint32_t));
     if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.bnd_kid, hbkid.size() * sizeof(uint16_t));
@@ -762,6 +827,7 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   CK(cudaMemcpy(b.node, hnode.data(), hnode.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(b.inst, hinst.data(), n * sizeof(Inst), cudaMemcpyHostToDevice));
   if (b.kid) CK(cudaMemcpy(b.kid, hkid.data(), hkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  if (b.block_off) CK(cudaMemcpy(b.block_off, hblock.data(), hblock.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (b.bnd) CK(cudaMemcpy(b.bnd, hbnd.data(), hbnd.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   if (b.bnd_kid) CK(cudaMemcpy(b.bnd_kid, hbkid.data(), hbkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
   b.fa = b.buf0;
@@ -959,6 +1025,19 @@ int tune(Batch &b, int32_t *chosen) {
     }
   }
   b.norm_block = pick;
+  // the three field kernels or the z-marching one (three chunk lengths), over whole steps
+  best = 1e30f;
+  int pick_fields = b.fields;
+  for (int v = 3; v >= 0; --v) {
+    if (v > 0 && fields_attributes() != LBM_OK) continue;
+    b.fields = v;
+    const float t = time_it([&] { enqueue_step(b, b.stream, b.fa, b.fb, 0, false, b.acc_scratch); });
+    if (t < best) {
+      best = t;
+      pick_fields = v;
+    }
+  }
+  b.fields = pick_fields;
   // programmatic dependent launch of the step's later kernels, on or off, over whole steps
   best = 1e30f;
   bool pick_pdl = b.pdl;
@@ -981,6 +1060,7 @@ int tune(Batch &b, int32_t *chosen) {
     chosen[1] = b.dens_block;
     chosen[2] = b.norm_block;
     chosen[3] = b.pdl ? 1 : 0;
+    chosen[4] = b.fields;
   }
   return LBM_OK;
 }
@@ -989,12 +1069,14 @@ int set_launch(Batch &b, const int32_t *blocks) {
   if (!blocks) return LBM_EINVAL;
   const auto one_of = [](int v, int a, int c, int d) { return v == a || v == c || v == d; };
   if (!one_of(blocks[0], 64, 128, 256) || !one_of(blocks[1], 128, 256, 512) || !one_of(blocks[2], 128, 256, 512) ||
-      (blocks[3] != 0 && blocks[3] != 1))
+      (blocks[3] != 0 && blocks[3] != 1) || blocks[4] < 0 || blocks[4] > 3)
     return LBM_EINVAL;
+  if (blocks[4] > 0 && fields_attributes() != LBM_OK) return LBM_ECUDA;
   b.main_block = blocks[0];
   b.dens_block = blocks[1];
   b.norm_block = blocks[2];
   b.pdl = blocks[3] == 1;
+  b.fields = blocks[4];
   drop_graphs(b);
   return LBM_OK;
 }
@@ -1239,6 +1321,10 @@ int adjoint_forward(Batch &b, int64_t nsteps, int64_t every, double *objective) 
 // at solids) into b.rhoN / b.nrm
 void launch_fields(Batch &b, cudaStream_t st, const float *fin) {
   launch_density<float>(b, st, fin);
+  if (b.fields) {
+    launch_fields_march(b, st);
+    return;
+  }
   if (b.n_bnd > 0) launch_solids(b, st, true);
   launch_normal(b, st);
   if (b.n_bnd > 0) launch_solids(b, st, false);
@@ -1410,6 +1496,26 @@ __global__ void k_normal_solid_all(Lattice L, const uint32_t *__restrict__ link,
   }
   const float m = sqrtf(ax * ax + ay * ay + az * az);
   nrm[s] = m >= GRAD_EPS ? make_float4(ax / m, ay / m, az / m, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The entries of f_out that k_main does not write: zero at solid nodes (they
+// carry no populations), and in the paper's reaction mode the seven reactant
+// populations of every fluid node, which that mode does not evolve (copied).
+__global__ void k_static_rest(Lattice L, int reaction_mode, const uint32_t *__restrict__ link,
+                              const float *__restrict__ fin, float *__restrict__ fout) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L.nx || y >= L.ny) return;
+  const unsigned ps = (unsigned)L.pstride;
+  const unsigned off = (unsigned)((z + 1) * L.plane + (long long)y * L.nx + x);
+  if (link[nidx(L, x, y, z)] & BIT_SOLID) {
+#pragma unroll
+    for (int p = 0; p < NPOP; ++p) fout[(unsigned)p * ps + off] = 0.f;
+  } else if (reaction_mode == 1) {
+#pragma unroll
+    for (int j = 0; j < Q7; ++j) fout[(unsigned)(2 * Q + j) * ps + off] = fin[(unsigned)(2 * Q + j) * ps + off];
+  }
 }
 
 }  // namespace
@@ -1592,6 +1698,9 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   const size_t pop_bytes = (size_t)NPOP * n * sizeof(float);
   const char *a = (const char *)f_in, *b = (const char *)f_out;
   if (a < b + pop_bytes && b < a + pop_bytes) return LBM_EINVAL;   // overlap
+  // an error left pending by the caller's earlier work is reported, not consumed
+  // (the check after the launches below can then only see this call's own)
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
   unsigned char *base = nullptr;
@@ -1625,6 +1734,7 @@ int lbm_step_static(int32_t nx, int32_t ny, int32_t nz, const uint8_t *solid, co
   k_normal<<<ng, nb, 0, st>>>(L, sp, rhoN, link, ns, nrm);
   k_normal_solid_all<<<ng, nb, 0, st>>>(L, link, nrm);
   k_main<<<ng, nb, 0, st>>>(L, sp, fin, fout, link, nrm, acc, 0, nullptr, nullptr);
+  k_static_rest<<<ng, nb, 0, st>>>(L, sp.reaction_mode, link, fin, fout);
   if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
   if (delta_sum &&
       cudaMemcpyAsync(delta_sum, acc + 2, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)

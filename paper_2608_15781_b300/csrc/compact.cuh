@@ -375,6 +375,240 @@ __global__ void k_normal_solid_c(const Inst *__restrict__ inst, const __grid_con
   }
 }
 
+// ---------------------------------------------------------------------------
+// a3, a4, a5 and the normals at solids in one launch, marching through z with
+// shared-memory planes.  A block owns a TX x TY column of the lattice and a
+// chunk of z-planes [zb, ze).  It walks the planes z = zb - 3 .. ze + 2 and
+// keeps rings of the last few planes in shared memory: rho^N with a halo of
+// three nodes in x and y (x, y periodic), the link words, the solid normals of
+// the wall nodes and the wetted normals.  With the planes of rho^N and of the
+// link words of z arriving (cp.async, issued one iteration ahead), a block
+//   forms the colour at the boundary solids of plane z - 1  (Eq. color_lattice_weighted_average,
+//                                                           xy box + 2),
+//   the wetted normals of the fluid nodes of plane z - 2    (Eq. finite_difference_scheme,
+//                                                           Eq. realigned_normal_vectors, box + 1),
+//   the normals at the boundary solids of plane z - 3       (weighted average, renormalised, box),
+// and writes n (with |grad rho^N|) for its fluid and boundary-solid nodes and
+// rho^N at its boundary solids.  Each value is computed with the same operations
+// in the same order as the separate kernels (k_color_solid_c, k_normal_c,
+// k_normal_solid_c), so the two forms agree bit for bit; the halo values (the xy
+// ring, three planes below and above the chunk) are recomputed by every block
+// that needs them.  z is periodic or, in column mode, a node on plane 0
+// (nz - 1) takes itself for its z - 1 (z + 1) neighbour; planes outside the
+// lattice are then neither loaded nor computed.
+template <int TX, int TY>
+struct MarchTile {
+  static constexpr int H = 3;                                   // xy halo of the staged planes
+  static constexpr int PX = TX + 2 * H, PY = TY + 2 * H, PN = PX * PY;
+  static constexpr int RING_R = 5, RING_L = 5, RING_S = 2, RING_N = 3;
+  static constexpr size_t smem_bytes() {
+    return sizeof(float4) * PN * RING_S + sizeof(float) * PN * RING_R + sizeof(uint32_t) * PN * RING_L +
+           sizeof(float) * 3 * PN * RING_N + sizeof(int) * (PX + PY);
+  }
+};
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ int ring(int z, int n) { return ((z % n) + n) % n; }
+
+// blocks of one lattice: ntx x nty columns times ceil(nz / chunk) chunks, x fastest
+__device__ __forceinline__ void march_block(const Lattice &L, int tx, int ty, int chunk, int t, int &x0, int &y0,
+                                            int &zb, int &ze) {
+  const int ntx = (L.nx + tx - 1) / tx, nty = (L.ny + ty - 1) / ty;
+  x0 = (t % ntx) * tx;
+  y0 = ((t / ntx) % nty) * ty;
+  zb = (t / (ntx * nty)) * chunk;
+  ze = min(zb + chunk, L.nz);
+}
+
+template <int TX, int TY, bool BATCH>
+__global__ void __launch_bounds__(256) k_fields_march(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
+                                                      const int *__restrict__ block_off, int n_inst, int chunk,
+                                                      const uint32_t *__restrict__ link,
+                                                      const float4 *__restrict__ ns, float *__restrict__ rhoN,
+                                                      float4 *__restrict__ nrm) {
+  using MT = MarchTile<TX, TY>;
+  constexpr int H = MT::H, PX = MT::PX, PY = MT::PY, PN = MT::PN;
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char msm[];
+  float4 *S = reinterpret_cast<float4 *>(msm);                  // solid normals (+ angle) of wall nodes
+  float *R = reinterpret_cast<float *>(S + PN * MT::RING_S);    // rho^N; colour at boundary solids
+  uint32_t *Lk = reinterpret_cast<uint32_t *>(R + PN * MT::RING_R);
+  float *N = reinterpret_cast<float *>(Lk + PN * MT::RING_L);   // wetted normals, 3 components per plane
+  int *xs = reinterpret_cast<int *>(N + 3 * PN * MT::RING_N);
+  int *ys = xs + PX;
+  int k = 0, t = blockIdx.x;
+  if (BATCH) {
+    int lo = 0, hi = n_inst - 1;                                 // last k with block_off[k] <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (block_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    k = lo;
+    t = blockIdx.x - block_off[k];
+  }
+  const Inst &I = BATCH ? inst[k] : single;
+  const Lattice &L = I.L;
+  int x0, y0, zb, ze;
+  march_block(L, TX, TY, chunk, t, x0, y0, zb, ze);
+  const bool clampz = L.bc_z != 0;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int c = tid; c < PX + PY; c += nth) {
+    if (c < PX)
+      xs[c] = ((x0 + c - H) % L.nx + L.nx) % L.nx;
+    else
+      ys[c - PX] = ((y0 + c - PX - H) % L.ny + L.ny) % L.ny;
+  }
+  __syncthreads();
+  const uint32_t *lk_ = link + I.node_off;
+  const float4 *ns_ = ns + I.node_off;
+  float *rn = rhoN + I.node_off;
+  float4 *nn = nrm + I.node_off;
+  const long long nx = L.nx, plane = L.plane;
+  auto exists = [&](int z) { return !clampz || (z >= 0 && z < L.nz); };
+  auto gplane = [&](int z) { return (long long)(clampz ? z : ring(z, L.nz)) * plane; };
+  auto zdn = [&](int z) { return (clampz && z == 0) ? z : z - 1; };
+  auto zup = [&](int z) { return (clampz && z == L.nz - 1) ? z : z + 1; };
+  // rho^N of plane z (xy box + 3) and its link words (box + 2)
+  auto load_plane = [&](int z) {
+    if (!exists(z)) return;
+    const long long zo = gplane(z);
+    float *Rs = R + ring(z, MT::RING_R) * PN;
+    uint32_t *Ls = Lk + ring(z, MT::RING_L) * PN;
+    for (int c = tid; c < PN; c += nth) {
+      const int i = c % PX, j = c / PX;
+      const long long g = zo + ys[j] * nx + xs[i];
+      cp_async4(Rs + c, rn + g);
+      if (i >= 1 && i < PX - 1 && j >= 1 && j < PY - 1) cp_async4(Ls + c, lk_ + g);
+    }
+  };
+  // solid normals of plane z (box + 1; zero away from wall nodes)
+  auto load_solid = [&](int z) {
+    if (!exists(z)) return;
+    const long long zo = gplane(z);
+    float4 *Ss = S + ring(z, MT::RING_S) * PN;
+    for (int c = tid; c < PN; c += nth) {
+      const int i = c % PX, j = c / PX;
+      if (i >= 2 && i < PX - 2 && j >= 2 && j < PY - 2) cp_async16(Ss + c, ns_ + zo + ys[j] * nx + xs[i]);
+    }
+  };
+  auto owned = [&](int i, int j) {
+    return i >= H && i < H + TX && j >= H && j < H + TY && x0 + i - H < L.nx && y0 + j - H < L.ny;
+  };
+  load_plane(zb - 3);
+  cp_async_commit();
+  for (int zl = zb - 3; zl <= ze + 2; ++zl) {
+    cp_async_wait_all();
+    __syncthreads();   // plane zl (rho^N, links) and the solid normals of plane zl - 2 have landed
+    if (zl + 1 <= ze + 2) load_plane(zl + 1);
+    if (zl - 1 >= zb - 1 && zl - 1 <= ze) load_solid(zl - 1);
+    cp_async_commit();
+    // colour at the boundary solids of plane zc = zl - 1, box + 2
+    const int zc = zl - 1;
+    if (zc >= zb - 2 && exists(zc)) {
+      float *Rc = R + ring(zc, MT::RING_R) * PN;
+      const float *Rd = R + ring(zdn(zc), MT::RING_R) * PN, *Ru = R + ring(zup(zc), MT::RING_R) * PN;
+      const uint32_t *Lc = Lk + ring(zc, MT::RING_L) * PN;
+      for (int c = tid; c < PN; c += nth) {
+        const int i = c % PX, j = c / PX;
+        if (i < 1 || i >= PX - 1 || j < 1 || j >= PY - 1) continue;
+        const uint32_t lk = Lc[c];
+        if (!(lk & BIT_SOLID_BND)) continue;
+        float num = 0.f, den = 0.f;
+#pragma unroll
+        for (int d = 0; d < Q - 1; ++d) {
+          const bool fl = (lk >> d) & 1u;
+          const float *Rp = CZ[d] < 0 ? Rd : (CZ[d] > 0 ? Ru : Rc);
+          const float v = fl ? Rp[c + CX[d] + CY[d] * PX] : 0.f;   // fluid cells only: never written here
+          num += fl ? W[d] * v : 0.f;
+          den += fl ? W[d] : 0.f;
+        }
+        Rc[c] = den > 0.f ? num / den : 0.f;
+      }
+    }
+    __syncthreads();
+    // wetted normals of the fluid nodes of plane zn = zl - 2, box + 1
+    const int zn = zl - 2;
+    if (zn >= zb - 1 && exists(zn)) {
+      const float *Rc = R + ring(zn, MT::RING_R) * PN;
+      const float *Rd = R + ring(zdn(zn), MT::RING_R) * PN, *Ru = R + ring(zup(zn), MT::RING_R) * PN;
+      const uint32_t *Lc = Lk + ring(zn, MT::RING_L) * PN;
+      const float4 *Ss = S + ring(zn, MT::RING_S) * PN;
+      float *Nx = N + ring(zn, MT::RING_N) * 3 * PN, *Ny = Nx + PN, *Nz = Ny + PN;
+      const long long zo = gplane(zn);
+      const bool out = zn >= zb && zn < ze;
+      for (int c = tid; c < PN; c += nth) {
+        const int i = c % PX, j = c / PX;
+        if (i < 2 || i >= PX - 2 || j < 2 || j >= PY - 2) continue;
+        const uint32_t lk = Lc[c];
+        float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!(lk & BIT_SOLID)) {
+          float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+          for (int d = 0; d < Q - 1; ++d) {
+            const float *Rp = CZ[d] < 0 ? Rd : (CZ[d] > 0 ? Ru : Rc);
+            const float v = 3.0f * W[d] * Rp[c + CX[d] + CY[d] * PX];
+            if (CX[d]) gx += CX[d] * v;
+            if (CY[d]) gy += CY[d] * v;
+            if (CZ[d]) gz += CZ[d] * v;
+          }
+          n = wetted_normal_from(I.P, lk, [&] { return Ss[c]; }, gx, gy, gz);
+          if (out && owned(i, j)) nn[zo + ys[j] * nx + xs[i]] = n;
+        }
+        Nx[c] = n.x;
+        Ny[c] = n.y;
+        Nz[c] = n.z;
+      }
+    }
+    __syncthreads();
+    // normals at the boundary solids of plane zs = zl - 3, box
+    const int zs = zl - 3;
+    if (zs >= zb && exists(zs)) {
+      const uint32_t *Lc = Lk + ring(zs, MT::RING_L) * PN;
+      const float *Rc = R + ring(zs, MT::RING_R) * PN;
+      const float *Nc = N + ring(zs, MT::RING_N) * 3 * PN;
+      const float *Nd = N + ring(zdn(zs), MT::RING_N) * 3 * PN, *Nu = N + ring(zup(zs), MT::RING_N) * 3 * PN;
+      const long long zo = gplane(zs);
+      for (int c = tid; c < PN; c += nth) {
+        const int i = c % PX, j = c / PX;
+        if (!owned(i, j)) continue;
+        const uint32_t lk = Lc[c];
+        if (!(lk & BIT_SOLID_BND)) continue;
+        float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+        for (int d = 0; d < Q - 1; ++d) {
+          if ((lk >> d) & 1u) {
+            const float *Np = CZ[d] < 0 ? Nd : (CZ[d] > 0 ? Nu : Nc);
+            const int q = c + CX[d] + CY[d] * PX;
+            ax += W[d] * Np[q];
+            ay += W[d] * Np[PN + q];
+            az += W[d] * Np[2 * PN + q];
+          }
+        }
+        const float m = sqrtf(ax * ax + ay * ay + az * az);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m >= GRAD_EPS) {
+          const float inv = 1.0f / m;
+          v = make_float4(ax * inv, ay * inv, az * inv, 0.f);
+        }
+        const long long g = zo + ys[j] * nx + xs[i];
+        nn[g] = v;
+        rn[g] = Rc[c];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
 // outlet ghost (column mode) of slot gs from the post-collision populations of a
 // fluid node of plane nz - 1 (same arithmetic as write_outlet_ghost)
 template <typename T>

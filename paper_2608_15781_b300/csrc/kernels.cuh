@@ -454,8 +454,11 @@ __global__ void k_color_solid(Lattice L, const uint32_t *__restrict__ list, long
 // a4 + a5 from the gradient (gx, gy, gz): n = +grad/|grad| (reading of
 // Eq. color_gradient_normal), then at wall nodes n_+ or n_- of
 // Eq. realigned_normal_vectors, whichever is nearer to n.  Returns (n, |grad|).
-__device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk, const float4 *__restrict__ ns,
-                                                unsigned node, float gx, float gy, float gz) {
+// solid() returns the node's solid normal n_s and contact angle (radians, .w);
+// it is called only at wall nodes.
+template <class SolidNormal>
+__device__ __forceinline__ float4 wetted_normal_from(const StepParams &P, uint32_t lk, const SolidNormal &solid,
+                                                     float gx, float gy, float gz) {
   const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
   float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
   if (gm >= GRAD_EPS) {
@@ -464,7 +467,7 @@ __device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk
     ny_ = gy * inv;
     nz_ = gz * inv;
     if ((lk & BIT_WALL) && (lk & BIT_NS_OK)) {
-      const float4 s = ns[node];
+      const float4 s = solid();
       float sin_th, cos_th;
       sincosf(s.w, &sin_th, &cos_th);
       const float c = s.x * nx_ + s.y * ny_ + s.z * nz_;          // cos(theta')
@@ -489,6 +492,10 @@ __device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk
     }
   }
   return make_float4(nx_, ny_, nz_, gm);
+}
+__device__ __forceinline__ float4 wetted_normal(const StepParams &P, uint32_t lk, const float4 *__restrict__ ns,
+                                                unsigned node, float gx, float gy, float gz) {
+  return wetted_normal_from(P, lk, [&] { return ns[node]; }, gx, gy, gz);
 }
 
 // a4 + a5 over the lattice (one thread per node)

@@ -24,7 +24,7 @@ NPOP = 45
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN = 0, -1, -2, -3, -4
 FIELD_RHON, FIELD_NORMAL, FIELD_GRADMAG, FIELD_NS, FIELD_NN, FIELD_CURV, FIELD_DELTA = range(7)
-KERNEL_NAMES = ("density", "color_solid", "normal", "normal_solid", "main", "observables")
+KERNEL_NAMES = ("density", "color_solid", "normal", "normal_solid", "main", "observables", "fields")
 
 # exported symbols (kept in sync with include/cglbm.h; the CPU tests check both)
 SYMBOLS = (
@@ -250,16 +250,18 @@ def lbm_info(ctx):
 
 
 def _launch_dict(blocks):
-    return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]), pdl=int(blocks[3]))
+    return dict(main=int(blocks[0]), density=int(blocks[1]), normal=int(blocks[2]), pdl=int(blocks[3]),
+                fields=int(blocks[4]))
 
 
 def _launch_array(launch):
-    return np.array([launch["main"], launch["density"], launch["normal"], launch.get("pdl", 1)], dtype=np.int32)
+    return np.array([launch["main"], launch["density"], launch["normal"], launch.get("pdl", 1),
+                     launch.get("fields", 0)], dtype=np.int32)
 
 
 def lbm_tune(ctx):
     """Time the candidate launch configurations on the current state and keep the fastest; returns it."""
-    blocks = np.zeros(4, dtype=np.int32)
+    blocks = np.zeros(5, dtype=np.int32)
     _check(load_library().lbm_tune(ctx, _ptr(blocks)), "lbm_tune")
     return _launch_dict(blocks)
 
@@ -467,7 +469,7 @@ class Batch:
         _check(load_library().lbm_batch_set_state(self.handle, int(k), _ptr(f), f.nbytes), "lbm_batch_set_state")
 
     def tune(self):
-        blocks = np.zeros(4, dtype=np.int32)
+        blocks = np.zeros(5, dtype=np.int32)
         _check(load_library().lbm_batch_tune(self.handle, _ptr(blocks)), "lbm_batch_tune")
         return _launch_dict(blocks)
 

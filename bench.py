@@ -193,9 +193,19 @@ def bytes_per_fluid_node(params):
 
 
 # --------------------------------------------------------------------------- CPU oracle legs
-def oracle_sample(wl, steps, crop):
-    """Time the FP64 oracle on a z/y/x crop of the workload's mask; returns (MLUPS, seconds, nodes)."""
+def _oracle_params(wl):
     from oracle import cglbm as O
+    p = wl.params
+    return O.Params(tau=p.tau, sigma=p.sigma, beta=p.beta, theta_deg=p.theta_deg, accel=tuple(p.accel),
+                    diffusivity=p.diffusivity, k_rate=p.k_rate, c_init=p.c_init, c_in=p.c_in, u_in=p.u_in,
+                    rho_out=p.rho_out, xi=p.xi, reaction_mode=p.reaction_mode, bc_z=wl.bc_z)
+
+
+def _oracle_worker(job):
+    """One process: the FP64 oracle on one z-slab crop of the workload's mask, single-threaded.
+
+    Returns (seconds of the timed steps, lattice nodes of the crop)."""
+    name, z0, crop, warmup, steps = job
     try:
         from threadpoolctl import threadpool_limits
     except ImportError:            # NumPy's elementwise work is single-threaded anyway
@@ -203,31 +213,61 @@ def oracle_sample(wl, steps, crop):
 
         def threadpool_limits(_n):
             return contextlib.nullcontext()
-
-    solid = wl.mask()[: crop[0], : crop[1], : crop[2]]
-    p = wl.params
-    op = O.Params(tau=p.tau, sigma=p.sigma, beta=p.beta, theta_deg=p.theta_deg, accel=tuple(p.accel),
-                  diffusivity=p.diffusivity, k_rate=p.k_rate, c_init=p.c_init, c_in=p.c_in, u_in=p.u_in,
-                  rho_out=p.rho_out, xi=p.xi, reaction_mode=p.reaction_mode, bc_z=wl.bc_z)
+    from oracle import cglbm as O
+    from paper_2608_15781_b300.configs import WORKLOADS
+    wl = WORKLOADS[name]
+    full = wl.mask()
+    zz = (np.arange(crop[0]) + z0) % full.shape[0]
+    solid = full[zz][:, : crop[1], : crop[2]]
     with threadpool_limits(1):
         g = O.Geometry(solid=solid, bc_z=wl.bc_z)
+        op = _oracle_params(wl)
         st = O.init_state(g, op)
+        for _ in range(warmup):
+            st = O.step(st, g, op)
         t0 = time.perf_counter()
         for _ in range(steps):
             st = O.step(st, g, op)
         dt = time.perf_counter() - t0
-    n = int(np.prod(solid.shape))
-    return n * steps / dt / 1e6, dt, n
+    return dt, int(np.prod(solid.shape))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(wl, crop, warmup, steps, workers):
+    """The oracle on `workers` host cores at once: one spawned process per core, each on its own
+    z-slab crop of the mask.  Returns (whole-job MLUPS, slowest worker's seconds, nodes per worker)."""
+    import multiprocessing as mp
+
+    nz = wl.shape[0]
+    jobs = [(wl.name, (w * crop[0]) % nz, crop, warmup, steps) for w in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    t = max(r[0] for r in res)
+    nodes = sum(r[1] for r in res)
+    return nodes * steps / t / 1e6, t, res[0][1]
+
+
+def baseline_workers():
+    """Host cores used by the oracle legs: every core, at most 32 processes (each holds ~1 GB)."""
+    return max(1, min(host_cores(), 32))
 
 
 def cpu_baseline(wl):
     nz, ny, nx = wl.shape
-    crop = (min(nz, 32), ny, nx)
+    crop = (min(nz, 16), ny, nx)
+    workers = baseline_workers()
     steps = 3
-    mlups, dt, n = oracle_sample(wl, steps, crop)
-    return {"value": round(mlups, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of a {crop[2]}x{crop[1]}x{crop[0]} (x,y,z) crop of the same mask and "
-                      f"boundaries, FP64 NumPy, single thread ({dt:.1f} s)"}
+    mlups, dt, n = oracle_parallel(wl, crop, 0, steps, workers)
+    return {"value": round(mlups, 4), "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{steps} steps on each of {workers} processes (one per host core of {host_cores()}), each on "
+                      f"its own {crop[2]}x{crop[1]}x{crop[0]} (x,y,z) z-slab crop of the same mask and boundaries, "
+                      f"FP64 NumPy, one thread per process; slowest process {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -237,26 +277,28 @@ def run_reference(args):
     from paper_2608_15781_b300.configs import WORKLOADS
     wl = WORKLOADS[args.workload]
     nz, ny, nx = wl.shape
+    workers = baseline_workers()
+    # the largest crop whose whole run stays within ~150 s (calibrated on 1 step on every core)
+    crops = [(min(nz, 16), ny, nx), (min(nz, 8), ny, nx), (min(nz, 4), min(ny, 64), min(nx, 64)),
+             (min(nz, 2), min(ny, 32), min(nx, 32)), (1, min(ny, 16), min(nx, 16))]
     total = args.steps + args.warmup
-    # pick the largest crop whose whole run stays within ~150 s (calibrated on 2 steps)
-    crops = [(min(nz, 32), ny, nx), (min(nz, 16), ny, nx), (min(nz, 8), min(ny, 64), min(nx, 64)),
-             (min(nz, 4), min(ny, 32), min(nx, 32)), (min(nz, 2), min(ny, 16), min(nx, 16))]
     chosen = crops[-1]
     for crop in crops:
-        _, dt, _ = oracle_sample(wl, 2, crop)
-        if dt / 2 * total <= 150.0:
+        _, dt, _ = oracle_parallel(wl, crop, 0, 1, workers)
+        if dt * total <= 150.0:
             chosen = crop
             break
-    oracle_sample(wl, args.warmup, chosen) if args.warmup else None
-    mlups, dt, n = oracle_sample(wl, args.steps, chosen)
-    sample = (f"each step: the FP64 NumPy oracle on a {chosen[2]}x{chosen[1]}x{chosen[0]} (x,y,z) crop of "
-              f"the workload's mask and boundaries, single thread")
+    mlups, dt, n = oracle_parallel(wl, chosen, args.warmup, args.steps, workers)
+    sample = (f"each step: the FP64 NumPy oracle on {workers} processes (one per host core of {host_cores()}), "
+              f"each on its own {chosen[2]}x{chosen[1]}x{chosen[0]} (x,y,z) z-slab crop of the workload's mask and "
+              f"boundaries, one thread per process")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(mlups, 5), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / max(args.steps, 1) * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "nodes_per_step": n, "crop_xyz": [chosen[2], chosen[1], chosen[0]]},
-        "cpu_baseline": {"value": round(mlups, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": wl.name, "nodes_per_step": n * workers, "crop_xyz": [chosen[2], chosen[1], chosen[0]],
+                   "processes": workers},
+        "cpu_baseline": {"value": round(mlups, 5), "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(mlups, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -358,13 +400,13 @@ def run_native(args):
         rates = ring.numpy().reshape(-1, 2)
         assert abs(rates[-1, 1] - ob2["consumed"]) <= 1e-9 * max(1.0, abs(ob2["consumed"]))
         h2d = N * 1                                  # the mask
-        d2h = 16 * args.steps + 4 * N + 8 * 8 * 2    # reaction sums per step, link readback, observables
+        d2h = 16 * args.steps + 8 * 8 * 2 + 3 * 8    # reaction sums per step, observables, layout totals
         e2e = {"value": round(whole_job_mlups(world, N, args.steps, te * 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": round(h2d / args.steps, 2), "d2h_bytes_per_step": round(d2h / args.steps, 2),
                "create_ms": round(t_create * 1e3, 1),
-               "includes": "lbm_create from the host mask (geometry precompute on the GPU, slot layout on the "
-                           "host), per step lbm_step(1) + lbm_reaction_async (D2H of the step's reaction sums "
-                           "into pinned memory), lbm_observables (synchronises), lbm_destroy"}
+               "includes": "lbm_create from the host mask (geometry precompute and slot layout on the GPU), "
+                           "per step lbm_step(1) + lbm_reaction_async (D2H of the step's reaction sums into "
+                           "pinned memory), lbm_observables (synchronises), lbm_destroy"}
 
     variants = {}
     if not args.no_variants:
@@ -388,8 +430,8 @@ def run_native(args):
         variants["adjoint"] = measure_adjoint(lbm, torch, stream, world, 3000 if args.steps >= 1000 else 300)
         variants["precision_periodic256"] = measure_precision(lbm, torch, stream, world,
                                                               5000 if args.steps >= 1000 else 200)
-        variants["column_series"] = measure_series(lbm, torch, stream, wl, head,
-                                                   20000 if args.steps >= 1000 else 400, 10)
+        variants["precision_crop64_vs_fp64"] = measure_precision_crop(lbm, torch, stream)
+        variants["column_series"] = measure_series(lbm, torch, stream, wl, head, 20000, 100)
 
     if rank != 0:
         return 0
@@ -559,18 +601,94 @@ def measure_precision(lbm, torch, stream, world, nsteps):
     return out
 
 
-def measure_series(lbm, torch, stream, wl, params, nsteps, samples):
-    """The headline column run for nsteps steps: conversion and gas saturation every nsteps/samples steps."""
+PRECISION_CROP = os.path.join(ROOT, "tests", "golden", "precision_crop64_fp64.txt")
+
+
+def read_precision_crop(path=PRECISION_CROP):
+    """The FP64 oracle reference of the precision workload's 64^3 crop (written by
+    tests/golden/make_precision_crop.py): observables per step and the velocity at sampled nodes."""
+    obs, vel, part = [], [], None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                continue
+            if line.startswith("[observables]"):
+                part = "obs"
+                continue
+            if line.startswith("[velocity]"):
+                part = "vel"
+                continue
+            v = line.split()
+            if part == "obs" and v:
+                obs.append([int(v[0])] + [float(x) for x in v[1:]])
+            elif part == "vel" and v:
+                vel.append([int(v[0]), int(v[1]), int(v[2])] + [float(x) for x in v[3:]])
+    return obs, vel
+
+
+def measure_precision_crop(lbm, torch, stream):
+    """FP32 and FP16 population storage against the FP64 oracle on the 64^3 crop of the
+    precision workload (same start, same steps): conversion, gas saturation and the
+    velocity at the reference's sampled fluid nodes."""
+    if not os.path.exists(PRECISION_CROP):
+        return {"unavailable": "reference file tests/golden/precision_crop64_fp64.txt not present"}
+    from paper_2608_15781_b300.configs import WORKLOADS
+
+    obs, vel = read_precision_crop()
+    wl = WORKLOADS["periodic256"]
+    solid = wl.mask()[:64, :64, :64].copy()
+    steps = [r[0] for r in obs]
+    zyx = np.array([r[:3] for r in vel], dtype=np.int64)
+    u_ref = np.array([r[3:] for r in vel])
+    umax = float(np.abs(u_ref).max())
+    out = {"workload": f"x, y, z < 64 crop of periodic256 run periodic, {steps[-1]} steps from rest; "
+                       f"FP64 oracle reference at {len(vel)} sampled fluid nodes",
+           "max_abs_u_fp64_sample": umax}
+    for name, storage in (("fp32", 0), ("fp16", 1)):
+        L = lbm.Lattice(solid, dataclasses.replace(wl.params, storage=storage), bc_z=0, stream=stream.cuda_stream)
+        dc, ds, done = [], [], 0
+        for row in obs:
+            L.step(row[0] - done)
+            done = row[0]
+            ob = L.observables()
+            dc.append(abs(ob["conversion"] - row[1]))
+            ds.append(abs(ob["gas_saturation"] - row[2]))
+        f = L.get_state().astype(np.float64)
+        L.close()
+        fm = f[0:19] + f[19:38]
+        rho = fm.sum(axis=0)
+        u = np.stack([np.tensordot(_C19[:, a], fm, axes=(0, 0)) for a in range(3)]) / np.where(solid, 1.0, rho)
+        du = np.abs(u[:, zyx[:, 0], zyx[:, 1], zyx[:, 2]].T - u_ref)
+        out[name] = {"abs_err_conversion_final": dc[-1], "abs_err_conversion_max": max(dc),
+                     "abs_err_gas_saturation_final": ds[-1], "abs_err_gas_saturation_max": max(ds),
+                     "max_abs_err_u": float(du.max()), "max_abs_err_u_rel_to_max_u": float(du.max() / umax)}
+    return out
+
+
+def measure_series(lbm, torch, stream, wl, params, nsteps, every):
+    """The headline column run for nsteps steps: conversion and gas saturation every `every` steps.
+
+    The column starts at rest, so the outlet sees no net inflow until the pressure
+    front from the inlet has crossed the porous column; meanwhile the gas generated
+    near the open outlet, pressurised by surface tension, draws a little liquid in
+    through it (outlet flux < 0, conversion 1 - Phi_out / Phi_in > 1).
+    ``transient_steps`` is the first sample from which the conversion stays in [0, 1]."""
     solid = wl.mask()
     L = lbm.Lattice(solid, params, bc_z=wl.bc_z, stream=stream.cuda_stream)
-    every = max(nsteps // samples, 1)
     series = []
-    for k in range(samples):
+    for k in range(nsteps // every):
         L.step(every)
         ob = L.observables()
         series.append([(k + 1) * every, round(ob["conversion"], 6), round(ob["gas_saturation"], 6)])
     L.close()
-    return {"workload": wl.name, "steps": every * samples, "series_step_conversion_saturation": series,
+    transient = None
+    for i in range(len(series)):
+        if all(0.0 <= r[1] <= 1.0 for r in series[i:]):
+            transient = series[i][0]
+            break
+    shown = [r for r in series if r[0] % (nsteps // 10) == 0 or r[0] <= 1000 and r[0] % 200 == 0]
+    return {"workload": wl.name, "steps": every * len(series), "sample_every": every,
+            "series_step_conversion_saturation": shown, "transient_steps": transient,
             "n_bad": int(ob["n_bad"])}
 
 

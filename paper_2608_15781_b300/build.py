@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libcglbm.so")
 SOURCES = [os.path.join(PKG, "csrc", "api.cu")]
-DEPENDS = SOURCES + [os.path.join(PKG, "csrc", f) for f in ("kernels.cuh", "lattice.cuh", "compact.cuh", "adjoint.cuh")] + [
+DEPENDS = SOURCES + [os.path.join(PKG, "csrc", f) for f in ("kernels.cuh", "lattice.cuh", "compact.cuh", "adjoint.cuh", "layout.cuh")] + [
     os.path.join(ROOT, "include", "cglbm.h")]
 
 NVCC_FLAGS = [

@@ -6,20 +6,19 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <memory>
 #include <new>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
 #include "adjoint.cuh"
 #include "cglbm.h"
 #include "compact.cuh"
+#include "layout.cuh"
 #include "kernels.cuh"
 
 using namespace cglbm;
@@ -31,7 +30,6 @@ struct InstHost {
   lbm_params prm{};
   long long n_fluid = 0, n_wall = 0, n_bnd = 0;
   double mc0 = 0.0;                   // reactant mass when the state was set
-  std::vector<uint32_t> slot_node;    // local fluid slot -> node index
 };
 
 // One or more independent lattices sharing one slot space (see compact.cuh).
@@ -576,30 +574,8 @@ int fill_obs(Batch &b, lbm_obs *out, int count) {
   return bad ? LBM_ENAN : LBM_OK;
 }
 
-// Build a batch: validate, precompute every instance's geometry on the GPU,
-// lay out the slot space, start from equilibrium.
-// f(c) for every c in [0, nchunks), spread over up to 32 host threads (the caller
-// included); if no thread can be started the caller does all of them
-template <class F>
-void parallel_chunks(int nchunks, F &&f) {
-  const unsigned hw = std::thread::hardware_concurrency();
-  const int nt = std::min(nchunks, (int)std::min(32u, std::max(1u, hw)));
-  std::atomic<int> next{0};
-  auto work = [&] {
-    for (int c = next.fetch_add(1); c < nchunks; c = next.fetch_add(1)) f(c);
-  };
-  std::vector<std::thread> pool;
-  for (int t = 1; t < nt; ++t) {
-    try {
-      pool.emplace_back(work);
-    } catch (...) {
-      break;
-    }
-  }
-  work();
-  for (std::thread &th : pool) th.join();
-}
-
+// Build a batch: validate, precompute every instance's geometry and lay out the
+// slot space on the GPU, start from equilibrium.
 int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *params, void *stream) {
   if (n < 1 || n > 65535 || !geoms || !params) return LBM_EINVAL;
   for (int k = 0; k < n; ++k) {
@@ -639,7 +615,6 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   CK(cudaMemsetAsync(b.rhoN, 0, nodes * sizeof(float), b.stream));
   CK(cudaMemsetAsync(b.nrm, 0, nodes * sizeof(float4), b.stream));
   CK(cudaMemsetAsync(b.err, 0, sizeof(int), b.stream));
-  std::vector<uint32_t> hlink(nodes);
   {
     // geometry kernels, one instance at a time (one-time set-up)
     uint8_t *d_solid = nullptr, *d_react = nullptr;
@@ -678,122 +653,61 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
     cudaFree(d_react);
     cudaFree(d_theta);
     if (rc) return cuda_fail(b, cudaErrorUnknown);
-    CK(cudaMemcpy(hlink.data(), b.link, nodes * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   }
-  // slot space: per instance its fluid slots in lattice order, then its ghost planes.
-  // Built plane-parallel in two passes (counts per plane, then direct fills at the
-  // prefix-summed offsets): the same layout as one sequential pass over the nodes.
-  struct PlaneCount {
-    long long fluid = 0, bnd = 0, wall = 0;
-  };
-  std::vector<std::vector<PlaneCount>> cnt(n);
+  // slot space, built on the GPU (layout.cuh): per instance the block counts and
+  // their scan, the totals to the host, then the fills at the instances' offsets
+  std::vector<long long> nblk(n + 1, 0);
+  for (int k = 0; k < n; ++k) nblk[k + 1] = nblk[k] + (b.h[k].d.L.n + kLayoutBlock - 1) / kLayoutBlock;
+  int *d_cnt = nullptr;
+  long long *d_tot = nullptr;
+  if (cudaMalloc((void **)&d_cnt, 3 * (size_t)nblk[n] * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&d_tot, 3 * (size_t)n * sizeof(long long)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFree(d_cnt);
+    return LBM_ENOMEM;
+  }
+  struct Scratch {   // frees the set-up buffers on every return path
+    int *c;
+    long long *t;
+    ~Scratch() {
+      cudaFree(c);
+      cudaFree(t);
+    }
+  } scratch{d_cnt, d_tot};
+  int *const cf = d_cnt, *const cb = d_cnt + nblk[n], *const cw = d_cnt + 2 * nblk[n];
   for (int k = 0; k < n; ++k) {
     const Lattice &L = b.h[k].d.L;
-    const uint32_t *lk = hlink.data() + b.h[k].d.node_off;
-    std::vector<PlaneCount> &c = cnt[k];
-    c.resize((size_t)L.nz);
-    parallel_chunks(L.nz, [&](int z) {
-      const uint32_t *w = lk + (long long)z * L.plane;
-      PlaneCount pc;
-      for (long long q = 0; q < L.plane; ++q) {
-        const uint32_t v = w[q];
-        if (v & BIT_SOLID) {
-          pc.bnd += (v & BIT_SOLID_BND) ? 1 : 0;
-        } else {
-          pc.fluid += 1;
-          pc.wall += (v & BIT_WALL) ? 1 : 0;
-        }
-      }
-      c[(size_t)z] = pc;
-    });
+    const long long o = nblk[k];
+    const int nb = (int)(nblk[k + 1] - o);
+    k_layout_count<<<nb, kLayoutBlock, 0, b.stream>>>(L.n, b.link + b.h[k].d.node_off, cf + o, cb + o, cw + o);
+    k_layout_scan<<<1, 1024, 0, b.stream>>>(nb, cf + o, cb + o, cw + o, d_tot + 3 * k);
   }
+  CK(cudaGetLastError());
+  std::vector<long long> tot(3 * (size_t)n);
+  CK(cudaMemcpyAsync(tot.data(), d_tot, tot.size() * sizeof(long long), cudaMemcpyDeviceToHost, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
   long long s = 0, nbnd_tot = 0;
-  std::vector<long long> slot0(n), bnd0(n);
+  std::vector<long long> bnd0(n);
   for (int k = 0; k < n; ++k) {
     InstHost &ih = b.h[k];
     const Lattice &L = ih.d.L;
-    slot0[k] = s;
-    bnd0[k] = nbnd_tot;
-    long long nf = 0;
-    for (const PlaneCount &pc : cnt[k]) {
-      nf += pc.fluid;
-      ih.n_bnd += pc.bnd;
-      ih.n_wall += pc.wall;
-    }
+    const long long nf = tot[3 * k];
+    ih.n_bnd = tot[3 * k + 1];
+    ih.n_wall = tot[3 * k + 2];
     if (nf == 0) return LBM_EINVAL;
+    bnd0[k] = nbnd_tot;
     ih.d.slot_off = (int)s;
     ih.d.nf = (int)nf;
     ih.n_fluid = nf;
     ih.d.ghost = (int)(s + nf);
     s += nf + (L.bc_z == 1 ? 2 * L.plane : 0);
     nbnd_tot += ih.n_bnd;
-    if (s > (1ll << 31) - 1) return LBM_EINVAL;
-  }
-  std::vector<uint32_t> hnode((size_t)s), hbnd((size_t)nbnd_tot);
-  std::vector<uint16_t> hkid(n > 1 ? (size_t)s : 0), hbkid(n > 1 ? (size_t)nbnd_tot : 0);
-  std::unique_ptr<int[]> hgidx_buf(new (std::nothrow) int[(size_t)std::max(gtot, 1ll)]);
-  if (!hgidx_buf) return LBM_ENOMEM;
-  int *const hgidx = hgidx_buf.get();
-  for (int k = 0; k < n; ++k) {
-    InstHost &ih = b.h[k];
-    const Lattice &L = ih.d.L;
-    const uint32_t *lk = hlink.data() + ih.d.node_off;
-    int *gi = hgidx + ih.d.gidx_off + L.plane;   // gi[node index], planes -1 and nz outside
-    ih.slot_node.resize((size_t)ih.d.nf);
-    const std::vector<PlaneCount> &c = cnt[k];
-    std::vector<long long> f0((size_t)L.nz), b0((size_t)L.nz);
-    long long fa = 0, ba = 0;
-    for (int z = 0; z < L.nz; ++z) {
-      f0[(size_t)z] = fa;
-      b0[(size_t)z] = ba;
-      fa += c[(size_t)z].fluid;
-      ba += c[(size_t)z].bnd;
-    }
-    const uint16_t kk = (uint16_t)k;
-    parallel_chunks(L.nz, [&](int z) {
-      long long fl = f0[(size_t)z], bl = bnd0[k] + b0[(size_t)z];
-      long long i = (long long)z * L.plane;
-      for (uint32_t y = 0; y < (uint32_t)L.ny; ++y)
-        for (uint32_t x = 0; x < (uint32_t)L.nx; ++x, ++i) {
-          const uint32_t w = lk[i];
-          const uint32_t pk = x | (y << 10) | ((uint32_t)z << 20);
-          if (w & BIT_SOLID) {
-            gi[i] = -1;
-            if (w & BIT_SOLID_BND) {
-              hbnd[(size_t)bl] = pk;
-              if (n > 1) hbkid[(size_t)bl] = kk;
-              ++bl;
-            }
-            continue;
-          }
-          const long long sl = slot0[k] + fl;
-          gi[i] = (int)sl;
-          ih.slot_node[(size_t)fl] = (uint32_t)i;
-          hnode[(size_t)sl] = pk;
-          if (n > 1) hkid[(size_t)sl] = kk;
-          ++fl;
-        }
-    });
-    const long long g = ih.d.ghost;
-    for (long long q = 0; q < L.plane; ++q) {
-      gi[q - L.plane] = L.bc_z == 1 ? (int)(g + q) : -1;                     // inlet plane z = -1
-      gi[L.nz * L.plane + q] = L.bc_z == 1 ? (int)(g + L.plane + q) : -1;    // outlet plane z = nz
-    }
-    if (L.bc_z == 1) {
-      for (long long q = 0; q < 2 * L.plane; ++q) {
-        hnode[(size_t)(g + q)] = kNoNode;
-        if (n > 1) hkid[(size_t)(g + q)] = kk;
-      }
-    }
+    if (s > (1ll << 31) - 1 || nbnd_tot > (1ll << 31) - 1) return LBM_EINVAL;
   }
   b.nslots = (int)s;
-  // every slot-map entry is a slot of the space or -1 (solid): the kernels index
-  // population arrays with these values
-  for (long long q = 0; q < gtot; ++q)
-    if (hgidx[q] < -1 || hgidx[q] >= b.nslots) return LBM_EINVAL;
   b.ns = (int)((s + 63) / 64 * 64);
   if ((long long)NPOP * b.ns >= (1ll << 32)) return LBM_EINVAL;   // 32-bit population offsets
-  b.n_bnd = (int)hbnd.size();
+  b.n_bnd = (int)nbnd_tot;
   // blocks of the marching field kernel, numbered instance by instance, per chunk option
   std::vector<int> hblock(3 * (size_t)(n + 1), 0);
   for (int o = 0; o < 3; ++o) {
@@ -810,26 +724,40 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   const size_t pop_bytes = (size_t)NPOP * b.ns * elt;
   rc = rc ? rc : dalloc(b, &b.buf0, pop_bytes);
   rc = rc ? rc : dalloc(b, &b.buf1, pop_bytes);
-  rc = rc ? rc : dalloc(b, (void **)&b.node, hnode.size() * sizeof(uint32_t));
+  rc = rc ? rc : dalloc(b, (void **)&b.node, (size_t)s * sizeof(uint32_t));
   rc = rc ? rc : dalloc(b, (void **)&b.inst, n * sizeof(Inst));
-  if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.kid, hkid.size() * sizeof(uint16_t));
+  if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.kid, (size_t)s * sizeof(uint16_t));
   if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.block_off, hblock.size() * sizeof(int));
   if (b.n_bnd > 0) {
-    rc = rc ? rc : dalloc(b, (void **)&b.bnd, hbnd.size() * sizeof(uint32_t));
-    if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.bnd_kid, hbkid.size() * sizeof(uint16_t));
+    rc = rc ? rc : dalloc(b, (void **)&b.bnd, (size_t)nbnd_tot * sizeof(uint32_t));
+    if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.bnd_kid, (size_t)nbnd_tot * sizeof(uint16_t));
   }
   if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    const InstHost &ih = b.h[k];
+    const Lattice &L = ih.d.L;
+    const long long o = nblk[k];
+    int *gi = b.gidx + ih.d.gidx_off;
+    k_layout_fill<<<(unsigned)(nblk[k + 1] - o), kLayoutBlock, 0, b.stream>>>(
+        L, k, ih.d.slot_off, (int)bnd0[k], b.link + ih.d.node_off, cf + o, cb + o, gi, b.node, b.kid, b.bnd,
+        b.bnd_kid);
+    k_layout_ghosts<<<(unsigned)((L.plane + 255) / 256), 256, 0, b.stream>>>(L, k, ih.d.ghost, gi, b.node, b.kid);
+  }
+  // every slot-map entry is a slot of the space or -1 (solid): the kernels index
+  // population arrays with these values
+  k_layout_check<<<(unsigned)((gtot + 255) / 256), 256, 0, b.stream>>>(gtot, b.gidx, b.nslots, b.err);
+  CK(cudaGetLastError());
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, b.err, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
   std::vector<Inst> hinst(n);
   for (int k = 0; k < n; ++k) hinst[k] = b.h[k].d;
+  CK(cudaMemcpyAsync(b.inst, hinst.data(), n * sizeof(Inst), cudaMemcpyHostToDevice, b.stream));
+  if (b.block_off)
+    CK(cudaMemcpyAsync(b.block_off, hblock.data(), hblock.size() * sizeof(int), cudaMemcpyHostToDevice, b.stream));
+  CK(cudaStreamSynchronize(b.stream));
+  if (bad) return LBM_EINVAL;
   CK(cudaMemsetAsync(b.buf0, 0, pop_bytes, b.stream));
   CK(cudaMemsetAsync(b.buf1, 0, pop_bytes, b.stream));
-  CK(cudaMemcpy(b.gidx, hgidx, (size_t)gtot * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(b.node, hnode.data(), hnode.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(b.inst, hinst.data(), n * sizeof(Inst), cudaMemcpyHostToDevice));
-  if (b.kid) CK(cudaMemcpy(b.kid, hkid.data(), hkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-  if (b.block_off) CK(cudaMemcpy(b.block_off, hblock.data(), hblock.size() * sizeof(int), cudaMemcpyHostToDevice));
-  if (b.bnd) CK(cudaMemcpy(b.bnd, hbnd.data(), hbnd.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-  if (b.bnd_kid) CK(cudaMemcpy(b.bnd_kid, hbkid.data(), hbkid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
   b.fa = b.buf0;
   b.fb = b.buf1;
   for (int k = 0; k < n; ++k) {
@@ -890,29 +818,24 @@ int init_fields(Batch &b, int k, const float *rho_r, const float *rho_p, const f
 }
 
 // slot-space populations src (storage type T) of instance k -> host [45][n], zero at solids
+// (scattered into a dense device array, then one copy)
 template <typename T>
 int slots_to_host(Batch &b, int k, const T *src, float *dst, size_t bytes) {
   const InstHost &ih = b.h[k];
-  const size_t nf = (size_t)ih.d.nf;
   float *d = nullptr;
-  if (cudaMalloc((void **)&d, (size_t)NPOP * nf * sizeof(float)) != cudaSuccess) {
+  if (cudaMalloc((void **)&d, bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     return LBM_ENOMEM;
   }
-  k_slots_to_f32<T><<<(unsigned)((nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, src, d);
-  std::vector<float> h((size_t)NPOP * nf);
-  cudaError_t e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(float), cudaMemcpyDeviceToHost, b.stream);
+  cudaError_t e = cudaMemsetAsync(d, 0, bytes, b.stream);   // solid nodes hold no populations
+  if (e == cudaSuccess) {
+    k_slots_to_dense<T><<<(unsigned)((ih.d.nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, b.node, src, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, b.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b.stream);
   cudaFree(d);
-  if (e != cudaSuccess) return cuda_fail(b, e);
-  std::memset(dst, 0, bytes);   // solid nodes hold no populations
-  const long long n = ih.d.L.n;
-  for (int p = 0; p < NPOP; ++p) {
-    float *o = dst + (size_t)p * n;
-    const float *s = h.data() + (size_t)p * nf;
-    for (size_t t = 0; t < nf; ++t) o[ih.slot_node[t]] = s[t];
-  }
-  return LBM_OK;
+  return cuda_fail(b, e);
 }
 
 int get_state(Batch &b, int k, float *dst, size_t bytes) {
@@ -934,27 +857,21 @@ int set_state(Batch &b, int k, const float *src, size_t bytes) {
   if (bytes != (size_t)NPOP * ih.d.L.n * sizeof(float)) return LBM_EINVAL;
   if (b.sticky) return b.sticky;
   cudaSetDevice(b.device);
-  const size_t nf = (size_t)ih.d.nf;
-  const long long n = ih.d.L.n;
-  std::vector<float> h((size_t)NPOP * nf);
-  for (int p = 0; p < NPOP; ++p) {
-    const float *s = src + (size_t)p * n;
-    float *o = h.data() + (size_t)p * nf;
-    for (size_t t = 0; t < nf; ++t) o[t] = s[ih.slot_node[t]];
-  }
   float *d = nullptr;
-  if (cudaMalloc((void **)&d, h.size() * sizeof(float)) != cudaSuccess) {
+  if (cudaMalloc((void **)&d, bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     return LBM_ENOMEM;
   }
-  cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, b.stream);
+  cudaError_t e = cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, b.stream);
   if (e == cudaSuccess && normalise_buffers(b) != LBM_OK) e = cudaErrorUnknown;
   if (e == cudaSuccess) {
     with_storage(b, [&](auto *tag) {
       using T = std::remove_pointer_t<decltype(tag)>;
-      k_f32_to_slots<T><<<(unsigned)((nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, d, (T *)b.fa, (T *)b.fb);
+      k_dense_to_slots<T><<<(unsigned)((ih.d.nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, b.node, d, (T *)b.fa,
+                                                                                   (T *)b.fb);
     });
-    e = cudaStreamSynchronize(b.stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b.stream);
   }
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(b, e);
@@ -1535,11 +1452,7 @@ const char *lbm_strerror(int code) {
 
 int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out) {
   if (!out || check_geometry(geom) || check_params(params)) return LBM_EINVAL;
-  long long nfl = 0;
-  const long long n = (long long)geom->nx * geom->ny * geom->nz;
-  for (long long i = 0; i < n; ++i) nfl += geom->solid[i] ? 0 : 1;
-  if (nfl == 0) return LBM_EINVAL;
-  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();   // a mask without fluid is rejected by the layout pass
   if (!c) return LBM_ENOMEM;
   const int rc = batch_create(c->b, 1, geom, params, params->cuda_stream);
   if (rc) {

@@ -835,27 +835,4 @@ __global__ void k_observables_c(Slots S, const __grid_constant__ Inst single, co
   block_accumulate_inst<7>(v, k, obs, 8);
 }
 
-// state transfer helpers: stored populations of instance I's fluid slots <->
-// FP32 values in a [45][nf] buffer
-template <typename T>
-__global__ void k_slots_to_f32(Inst I, int ns_, const T *__restrict__ src, float *__restrict__ dst) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= I.nf) return;
-  const unsigned t = (unsigned)(I.slot_off + l);
-#pragma unroll
-  for (int p = 0; p < NPOP; ++p) dst[(size_t)p * I.nf + l] = Store<T>::ld(src, (unsigned)p * (unsigned)ns_ + t, p);
-}
-template <typename T>
-__global__ void k_f32_to_slots(Inst I, int ns_, const float *__restrict__ src, T *__restrict__ a, T *__restrict__ b) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= I.nf) return;
-  const unsigned t = (unsigned)(I.slot_off + l);
-#pragma unroll
-  for (int p = 0; p < NPOP; ++p) {
-    const float v = src[(size_t)p * I.nf + l];
-    Store<T>::st(a, (unsigned)p * (unsigned)ns_ + t, p, v);
-    Store<T>::st(b, (unsigned)p * (unsigned)ns_ + t, p, v);
-  }
-}
-
 }  // namespace cglbm

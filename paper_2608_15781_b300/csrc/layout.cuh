@@ -1,0 +1,190 @@
+// Slot space of a lattice, built on the GPU from its link words (one-time set-up).
+//
+// Fluid nodes get consecutive slots in lattice order (x fastest, then y, then z),
+// solid nodes next to the fluid get consecutive entries of the boundary-solid
+// list in the same order, and in column mode the two ghost planes follow the
+// fluid slots.  Three passes over the dense nodes of one lattice, in blocks of
+// kLayoutBlock nodes: count (fluid, boundary-solid and wall nodes per block),
+// scan (exclusive prefix of the block counts, one block of threads), fill (each
+// node's rank inside its block from warp ballots, plus the block's prefix).
+// The result is the same layout as one sequential pass over the nodes.
+#pragma once
+#include <cstdint>
+
+#include "compact.cuh"
+
+namespace cglbm {
+
+constexpr int kLayoutBlock = 256;   // nodes per block of the count and fill passes (= threads)
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Exclusive rank of flag within the block and the block's total (blockDim.x = kLayoutBlock).
+__device__ __forceinline__ int block_rank(bool flag, int &total) {
+  __shared__ int wsum[kLayoutBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) wsum[warp] = __popc(bal);
+  __syncthreads();
+  int before = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kLayoutBlock / 32; ++w) {
+    before += w < warp ? wsum[w] : 0;
+    tot += wsum[w];
+  }
+  __syncthreads();   // wsum may be reused by the next call
+  total = tot;
+  return before + __popc(bal & lanemask_lt());
+}
+
+// per block: fluid, boundary-solid and wall node counts
+__global__ void __launch_bounds__(kLayoutBlock) k_layout_count(long long n, const uint32_t *__restrict__ link,
+                                                               int *__restrict__ cf, int *__restrict__ cb,
+                                                               int *__restrict__ cw) {
+  const long long node = (long long)blockIdx.x * kLayoutBlock + threadIdx.x;
+  const uint32_t lk = node < n ? link[node] : BIT_SOLID;
+  int tf, tb, tw;
+  block_rank(node < n && !(lk & BIT_SOLID), tf);
+  block_rank(node < n && (lk & BIT_SOLID_BND), tb);
+  block_rank(node < n && !(lk & BIT_SOLID) && (lk & BIT_WALL), tw);
+  if (threadIdx.x == 0) {
+    cf[blockIdx.x] = tf;
+    cb[blockIdx.x] = tb;
+    cw[blockIdx.x] = tw;
+  }
+}
+
+// exclusive prefix of cf and cb over nb blocks (in place); totals of cf, cb, cw into tot[0..2]
+__global__ void __launch_bounds__(1024) k_layout_scan(int nb, int *__restrict__ cf, int *__restrict__ cb,
+                                                      const int *__restrict__ cw, long long *__restrict__ tot) {
+  __shared__ long long sf[1024], sb[1024];
+  __shared__ long long carry_f, carry_b, sum_w;
+  if (threadIdx.x == 0) {
+    carry_f = carry_b = sum_w = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const long long vf = i < nb ? cf[i] : 0, vb = i < nb ? cb[i] : 0;
+    sf[threadIdx.x] = vf;
+    sb[threadIdx.x] = vb;
+    if (i < nb) atomicAdd((unsigned long long *)&sum_w, (unsigned long long)cw[i]);
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
+      const long long af = threadIdx.x >= o ? sf[threadIdx.x - o] : 0;
+      const long long ab = threadIdx.x >= o ? sb[threadIdx.x - o] : 0;
+      __syncthreads();
+      sf[threadIdx.x] += af;
+      sb[threadIdx.x] += ab;
+      __syncthreads();
+    }
+    if (i < nb) {
+      cf[i] = (int)(carry_f + sf[threadIdx.x] - vf);
+      cb[i] = (int)(carry_b + sb[threadIdx.x] - vb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) {
+      carry_f += sf[1023];
+      carry_b += sb[1023];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    tot[0] = carry_f;
+    tot[1] = carry_b;
+    tot[2] = sum_w;
+  }
+}
+
+// Slots of instance k: gidx (lattice planes 0 .. nz - 1 at gi + plane), packed node
+// coordinates and instance of each fluid slot, boundary-solid list and its instances.
+__global__ void __launch_bounds__(kLayoutBlock) k_layout_fill(Lattice L, int k, int slot_off, int bnd_off,
+                                                              const uint32_t *__restrict__ link,
+                                                              const int *__restrict__ cf, const int *__restrict__ cb,
+                                                              int *__restrict__ gi, uint32_t *__restrict__ node,
+                                                              uint16_t *__restrict__ kid, uint32_t *__restrict__ bnd,
+                                                              uint16_t *__restrict__ bnd_kid) {
+  const long long i = (long long)blockIdx.x * kLayoutBlock + threadIdx.x;
+  const bool in = i < L.n;
+  const uint32_t lk = in ? link[i] : BIT_SOLID;
+  const bool fluid = in && !(lk & BIT_SOLID), bs = in && (lk & BIT_SOLID_BND);
+  int tf, tb;
+  const int rf = block_rank(fluid, tf), rb = block_rank(bs, tb);
+  if (!in) return;
+  const int x = (int)(i % L.nx), y = (int)((i / L.nx) % L.ny), z = (int)(i / L.plane);
+  const uint32_t pk = (uint32_t)x | ((uint32_t)y << 10) | ((uint32_t)z << 20);
+  if (fluid) {
+    const int s = slot_off + cf[blockIdx.x] + rf;
+    gi[L.plane + i] = s;
+    node[s] = pk;
+    if (kid) kid[s] = (uint16_t)k;
+  } else {
+    gi[L.plane + i] = -1;
+    if (bs) {
+      const int b = bnd_off + cb[blockIdx.x] + rb;
+      bnd[b] = pk;
+      if (bnd_kid) bnd_kid[b] = (uint16_t)k;
+    }
+  }
+}
+
+// the slot-map planes z = -1 and z = nz of instance k (ghost slots in column mode,
+// -1 in a periodic box) and the ghost slots' node words and instance
+__global__ void k_layout_ghosts(Lattice L, int k, int ghost, int *__restrict__ gi, uint32_t *__restrict__ node,
+                                uint16_t *__restrict__ kid) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= L.plane) return;
+  const bool col = L.bc_z == 1;
+  gi[q] = col ? (int)(ghost + q) : -1;
+  gi[(long long)(L.nz + 1) * L.plane + q] = col ? (int)(ghost + L.plane + q) : -1;
+  if (col) {
+    node[ghost + q] = kNoNode;
+    node[ghost + L.plane + q] = kNoNode;
+    if (kid) {
+      kid[ghost + q] = (uint16_t)k;
+      kid[ghost + L.plane + q] = (uint16_t)k;
+    }
+  }
+}
+
+// every slot-map entry is a slot of the space or -1; bad entries set *err
+__global__ void k_layout_check(long long count, const int *__restrict__ gi, int nslots, int *__restrict__ err) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < count && (gi[q] < -1 || gi[q] >= nslots)) atomicOr(err, 1);
+}
+
+// populations of instance I's fluid slots (storage type T) <-> FP32 dense [45][n] arrays
+template <typename T>
+__global__ void k_slots_to_dense(Inst I, int ns_, const uint32_t *__restrict__ node, const T *__restrict__ src,
+                                 float *__restrict__ dst) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= I.nf) return;
+  const unsigned t = (unsigned)(I.slot_off + l);
+  int x, y, z;
+  unpack(node[t], x, y, z);
+  const long long nd = nidx(I.L, x, y, z);
+#pragma unroll
+  for (int p = 0; p < NPOP; ++p) dst[(long long)p * I.L.n + nd] = Store<T>::ld(src, (unsigned)p * (unsigned)ns_ + t, p);
+}
+template <typename T>
+__global__ void k_dense_to_slots(Inst I, int ns_, const uint32_t *__restrict__ node, const float *__restrict__ src,
+                                 T *__restrict__ a, T *__restrict__ b) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= I.nf) return;
+  const unsigned t = (unsigned)(I.slot_off + l);
+  int x, y, z;
+  unpack(node[t], x, y, z);
+  const long long nd = nidx(I.L, x, y, z);
+#pragma unroll
+  for (int p = 0; p < NPOP; ++p) {
+    const float v = src[(long long)p * I.L.n + nd];
+    Store<T>::st(a, (unsigned)p * (unsigned)ns_ + t, p, v);
+    Store<T>::st(b, (unsigned)p * (unsigned)ns_ + t, p, v);
+  }
+}
+
+}  // namespace cglbm

@@ -4,8 +4,11 @@
      (recolouring of Eq. operator_recoloring with n along +grad rho^N).
   P2 Laplace law: dp = sigma / R for a cylindrical r-droplet and p-bubble, the
      higher pressure inside both (Eq. continuum_surface_force, Eq. interface_curvature);
-     the discrete curvature of smooth spherical and cylindrical colour fields is
-     2/R and 1/R, the same along every axis.
+     dp = 2 sigma / R for a spherical droplet and bubble; the discrete curvature
+     of smooth spherical and cylindrical colour fields is 2/R and 1/R, the same
+     along every axis.
+  P3 contact angle on a flat wall (60, 90, 120, 150 degrees) and the wetting
+     rotation itself at 30 - 150 degrees (Eq. realigned_normal_vectors).
   P4 Poiseuille: body-force channel flow between halfway bounce-back walls; the
      bulk second difference of u_x is -a/nu with nu = c_s^2 (tau - 1/2)
      (Eq. kinematic_viscosity) and the centre-line value is a H^2 / (8 nu).
@@ -130,6 +133,43 @@ def test_laplace_law_cylinder(R0, inverse):
     dp, ref = _laplace(R0, inverse)
     assert dp > 0                       # higher pressure inside, for a droplet and for a bubble
     assert abs(dp / ref - 1) < 0.05
+
+
+def _laplace_sphere(R0, inverse, n=40, sigma=0.02, steps=400, avg_from=200):
+    """Time-averaged dp / (2 sigma / R) of a spherical droplet (bubble) started with the
+    Laplace jump in density already inside, so that the start-up sound wave is small."""
+    shape = (n, n, n)
+    g = O.Geometry(solid=np.zeros(shape, bool), bc_z=0)
+    p = O.Params(sigma=sigma, k_rate=0.0)
+    z, y, x = np.mgrid[0:n, 0:n, 0:n]
+    c = n / 2 - 0.5
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    phi = np.tanh((R0 - r) / 2.0)
+    rho = 1.0 + (3 * 2 * sigma / R0) * (1 + phi) / 2
+    if inverse:
+        phi = -phi
+    st = O.init_state(g, p, rho_r=rho * (1 + phi) / 2, rho_p=rho * (1 - phi) / 2)
+    ratios = []
+    for k in range(1, steps + 1):
+        st, fl = O.step(st, g, p, return_fields=True)
+        if k >= avg_from and k % 10 == 0:
+            rho_m = fl.rho_r + fl.rho_p
+            inner = ((1 + fl.rhoN) / 2 if not inverse else (1 - fl.rhoN) / 2).sum()
+            R = (inner * 3 / (4 * math.pi)) ** (1 / 3)
+            dp = (rho_m[r < R - 4].mean() - rho_m[r > R + 4].mean()) * O.CS2
+            ratios.append(dp / (2 * sigma / R))
+    return float(np.mean(ratios)), float(np.min(ratios))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("inverse", [False, True])
+def test_laplace_law_sphere(inverse):
+    """A spherical r-droplet and p-bubble of radius 10 in a 40^3 box: dp = 2 sigma / R within 5 %
+    (measured +4.5 %; +7 % at R = 8, falling as 1/R^2 with the interface width), higher
+    pressure inside both."""
+    mean, lowest = _laplace_sphere(10, inverse)
+    assert lowest > 0
+    assert abs(mean - 1) < 0.05
 
 
 # --------------------------------------------------------------------- P4
@@ -307,23 +347,64 @@ def _fit_circle(px, pz):
     return xc, zc, math.sqrt(c + xc ** 2 + zc ** 2)
 
 
-@pytest.mark.parametrize("theta", [60.0, 120.0])
-def test_contact_angle_flat_wall(theta):
+@pytest.mark.parametrize("theta", [30.0, 60.0, 90.0, 120.0, 150.0])
+def test_wetting_rotation_is_the_geometric_rotation(theta):
+    """Eq. realigned_normal_vectors with the nearer candidate: wherever it applies, the wetted
+    normal is n rotated in the plane of n and n_s to the angle theta from n_s,
+    cos(theta) n_s + sin(theta) t / |t| with t = n - (n . n_s) n_s (so |n_wet| = 1 and
+    n_wet . n_s = cos(theta)); elsewhere n is unchanged."""
+    rng = np.random.default_rng(int(theta))
+    shape = (9, 8, 10)
+    solid = rng.random(shape) < 0.35
+    g = O.Geometry(solid=solid, bc_z=0)
+    n = rng.standard_normal((3,) + shape)
+    n /= np.sqrt((n * n).sum(axis=0))
+    n[:, rng.random(shape) < 0.1] = 0.0                     # some nodes without an interface
+    out = O.wetting(n, g, O.Params(theta_deg=theta))
+    c = (g.ns * n).sum(axis=0)
+    t = n - c * g.ns
+    tm = np.sqrt((t * t).sum(axis=0))
+    ok = g.ns_ok & (tm * tm >= 1e-6)
+    assert ok.sum() > 50
+    th = math.radians(theta)
+    want = math.cos(th) * g.ns + math.sin(th) * t / np.where(tm > 0, tm, 1.0)
+    assert np.abs(out - want)[:, ok].max() < 1e-12
+    assert np.abs((out * out).sum(axis=0) - 1.0)[ok].max() < 1e-12
+    assert np.abs((out * g.ns).sum(axis=0) - math.cos(th))[ok].max() < 1e-12
+    assert np.abs(out - n)[:, ~ok].max() == 0.0
+
+
+def _cap(nx, nz, theta0, area):
+    """rho^N of a cylindrical cap of the given area on the wall plane z = 1/2 meeting it at theta0."""
+    th = math.radians(theta0)
+    R = math.sqrt(area / (th - math.sin(th) * math.cos(th)))
+    zc = 0.5 - R * math.cos(th)
+    z, x = np.mgrid[0:nz, 0:nx].astype(float)
+    return np.tanh((R - np.sqrt((x - nx / 2) ** 2 + (z - zc) ** 2)) / 2.0)[:, None, :]
+
+
+@pytest.mark.parametrize("theta,start,nx,nz,tol", [(60.0, 90.0, 48, 26, 3.0), (90.0, 90.0, 48, 26, 3.0),
+                                                   (120.0, 90.0, 48, 26, 3.0), (150.0, 130.0, 64, 36, 8.0)])
+def test_contact_angle_flat_wall(theta, start, nx, nz, tol):
     """A cylindrical r-cap on a flat wall relaxes to the imposed angle, measured through r.
 
     Wetting scheme of Sec. 2.2 (Eq. realigned_normal_vectors, Eq. normal_vector_solid).
-    The cap starts as a half-disc (90 degrees); the angle of the fitted circle
-    with the halfway wall plane must come within 3 degrees of theta.
+    The cap starts at another angle (a half-disc of radius 10; for 150 degrees a
+    130-degree cap of area 300); the angle of the circle fitted to
+    its rho^N = 0 line with the halfway wall plane must come within 3 degrees of
+    theta.  At 150 degrees a cap of this size (radius about 10, contact region
+    about 10 nodes wide, comparable to the interface width) settles at 157.6 degrees
+    from above and below; a cap of twice the radius reaches 153 degrees, so the
+    bound there is 8 degrees.  30 degrees needs a cap too wide and flat for a CPU
+    pin (height 4 nodes at this area); the wetting rotation itself is pinned at
+    every angle above.
     """
-    nx, nz, R0 = 48, 26, 10.0
     shape = (nz, 1, nx)
     solid = np.zeros(shape, bool)
     solid[0] = solid[-1] = True
     g = O.Geometry(solid=solid, bc_z=0)
     p = O.Params(sigma=0.02, theta_deg=theta, k_rate=0.0, tau=0.7)
-    z, x = np.mgrid[0:nz, 0:nx].astype(float)
-    r = np.sqrt((x - nx / 2) ** 2 + (z - 0.5) ** 2)
-    phi = np.tanh((R0 - r) / 2.0)[:, None, :]
+    phi = _cap(nx, nz, start, math.pi * 100.0 / 2 if start == 90.0 else 300.0)
     st = O.init_state(g, p, rho_r=(1 + phi) / 2, rho_p=(1 - phi) / 2)
     st, fl = _run(st, g, p, 2000)
     rN = np.where(g.fluid, fl.rhoN, np.nan)[:, 0, :]
@@ -341,4 +422,4 @@ def test_contact_angle_flat_wall(theta):
     pts = np.array(pts)
     xc, zc, R = _fit_circle(pts[:, 0], pts[:, 1])
     measured = math.degrees(math.acos((0.5 - zc) / R))
-    assert abs(measured - theta) < 3.0
+    assert abs(measured - theta) < tol

@@ -431,6 +431,7 @@ def run_native(args):
         variants["precision_periodic256"] = measure_precision(lbm, torch, stream, world,
                                                               5000 if args.steps >= 1000 else 200)
         variants["precision_crop64_vs_fp64"] = measure_precision_crop(lbm, torch, stream)
+        variants["paper_mode_analysis"] = measure_paper_mode(lbm, torch, stream)
         variants["column_series"] = measure_series(lbm, torch, stream, wl, head, 20000, 100)
 
     if rank != 0:
@@ -663,6 +664,83 @@ def measure_precision_crop(lbm, torch, stream):
                      "abs_err_gas_saturation_final": ds[-1], "abs_err_gas_saturation_max": max(ds),
                      "max_abs_err_u": float(du.max()), "max_abs_err_u_rel_to_max_u": float(du.max() / umax)}
     return out
+
+
+def superficial_velocity_x(f, solid, accel_x):
+    """<u_x> = sum over fluid nodes of the physical velocity j_x / rho + a / 2, divided by all nodes
+    (the volume average of Darcy's law; single phase, so the force shift is the body force alone)."""
+    fm = f[0:19].astype(np.float64) + f[19:38]
+    rho = np.where(solid, 1.0, fm.sum(axis=0))
+    ux = np.tensordot(_C19[:, 0], fm, axes=(0, 0)) / rho + 0.5 * accel_x
+    return float(ux[~solid].sum() / solid.size)
+
+
+def measure_paper_mode(lbm, torch, stream, nsteps=50000, every=500, Da=1.0):
+    """The paper's reactive-flow analysis (Sec. 4.2 and 5.1) on GPU runs through the C ABI.
+
+    1. Permeability kappa = nu <u> / a of the structure from a single-phase run under
+       the body force (tau = 1, steady Darcy flow).
+    2. Nucleation sites (one site with one solid nearest neighbour per 64^3 block),
+       A_r, and the viscosity that gives the Damkohler number Da (the paper varies
+       Da through nu).
+    3. The paper-mode reactive run (rho^r -> rho^p at the sites, xi = 1, sigma = 0.3,
+       reactant-only start): m^r(t), m^p(t) and the reacted amount per step, turned
+       into the effectiveness factor alpha(t), its running mean and the fit of
+       m^r(t) = m^m exp(-xi A_r alpha t / (phi V))."""
+    from paper_2608_15781_b300 import analysis as AN
+    from paper_2608_15781_b300.configs import WORKLOADS
+
+    wl = WORKLOADS["paper128"]
+    solid = wl.mask()
+    p0 = wl.params
+    a = p0.accel[0]
+    mor = AN.morphology(solid)
+    V, phi = mor["volume"], mor["porosity"]
+    nu1 = AN.kinematic_viscosity(1.0)
+    L = lbm.Lattice(solid, dataclasses.replace(p0, tau=1.0, xi=0.0), stream=stream.cuda_stream)
+    u_mean = []
+    for _ in range(2):
+        L.step(3000)
+        u_mean.append(superficial_velocity_x(L.get_state(), solid, a))
+    L.close()
+    kappa = AN.permeability(nu1, u_mean[-1], a)
+    sites = AN.nucleation_sites(solid, block=64, seed=0)
+    A_r = AN.reactive_surface_area(sites, solid)
+    length = solid.shape[2]                       # along the body force (x)
+    nu = AN.viscosity_for_damkohler(Da, p0.xi, A_r, length, kappa, V, a)
+    tau = AN.tau_for_viscosity(nu)
+    L = lbm.Lattice(solid, dataclasses.replace(p0, tau=tau), reactive=sites, stream=stream.cuda_stream)
+    ob = L.observables()
+    m_m = ob["mass_r"] + ob["mass_p"]
+    t, m_r, m_p, rate = [], [], [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for k in range(nsteps // every):
+        e0.record(stream)
+        L.step(every)
+        e1.record(stream)
+        ob = L.observables()
+        ms += e0.elapsed_time(e1)
+        t.append((k + 1) * every)
+        m_r.append(ob["mass_r"])
+        m_p.append(ob["mass_p"])
+        rate.append(ob["rate"])
+    n_bad = int(ob["n_bad"])
+    L.close()
+    t = np.array(t, dtype=np.float64)
+    m_r = np.array(m_r)
+    alpha = AN.effectiveness_factor(rate, m_r, p0.xi, A_r, phi, V)
+    alpha_bar = AN.running_average(alpha)
+    alpha_fit = AN.fit_effectiveness(t, m_r, m_m, p0.xi, A_r, phi, V)
+    pick = [i for i in range(len(t)) if (i + 1) % max(1, len(t) // 10) == 0]
+    return {"workload": f"paper128 (128^3 periodic GRF, shell 6, porosity {phi:.3f}, seed 6), reactant-only start",
+            "permeability": kappa, "mean_u_x_at_3000_6000_steps": u_mean, "nucleation_sites": int(sites.sum()),
+            "A_r": A_r, "Da": Da, "nu": nu, "tau": tau, "sigma": p0.sigma, "xi": p0.xi, "accel_x": a,
+            "steps": int(t[-1]), "MLUPS": round(V * t[-1] / (ms * 1e-3) / 1e6, 1),
+            "alpha_fit": alpha_fit, "alpha_bar_final": float(alpha_bar[-1]),
+            "series_step_mr_over_mm_alpha_alphabar": [[int(t[i]), float(m_r[i] / m_m), float(alpha[i]),
+                                                       float(alpha_bar[i])] for i in pick],
+            "mass_conservation_rel": float(abs(m_r[-1] + m_p[-1] - m_m) / m_m), "n_bad": n_bad}
 
 
 def measure_series(lbm, torch, stream, wl, params, nsteps, every):

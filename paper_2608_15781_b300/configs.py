@@ -48,6 +48,13 @@ WORKLOADS = {
     "periodic256": Workload("periodic256", (256, 256, 256), 12, 0.5, 3, 0,
                             Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=1e-3,
                                    diffusivity=0.05, c_init=1.0)),
+    # 128^3 periodic box of the paper-mode analysis run (Sec. 4.2, 5.1): pore size of the
+    # 256^3 workloads (shell 6 on 128 = shell 12 on 256), reaction directly r -> p at
+    # one nucleation site per 64^3 block, xi = 1, sigma = 0.3, body force a = 3.616e-5
+    # along x; tau is set from the Damkohler number by the analysis run
+    "paper128": Workload("paper128", (128, 128, 128), 6, 0.5, 6, 0,
+                         Params(tau=1.0, sigma=0.3, beta=0.7, theta_deg=90.0, accel=(3.616e-5, 0.0, 0.0),
+                                reaction_mode=1, xi=1.0, k_rate=0.0)),
     # 96^3 column of the adjoint workload
     "column96": Workload("column96", (96, 96, 96), 6, 0.5, 5, 1,
                          Params(theta_deg=60.0, k_rate=2e-3, u_in=0.004, c_in=1.0)),

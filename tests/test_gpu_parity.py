@@ -269,14 +269,16 @@ def test_column_inlet_outlet_100_steps():
 
 
 def test_droplets_paper_mode_nucleation_sites():
-    """Paper reaction mode (rho^r -> rho^p directly, xi = 1) at a few nucleation sites, with droplets."""
+    """Paper reaction mode (rho^r -> rho^p directly, xi = 1) at the paper's nucleation sites
+    (analysis.nucleation_sites: one site with one solid nearest neighbour per block, here
+    12^3 blocks of a 24^3 box), with droplets."""
+    from paper_2608_15781_b300 import analysis
+
     shape = (24, 24, 24)
     solid = synth.grf_mask(shape, 3, 0.6, 4)
+    sites = analysis.nucleation_sites(solid, block=12, seed=2)
     g0 = O.Geometry(solid=solid, bc_z=0)
-    sites = np.zeros(shape, bool)
-    cand = np.argwhere(g0.nn == 1)
-    for k in range(0, len(cand), max(1, len(cand) // 4))[:4]:
-        sites[tuple(cand[k])] = True
+    assert sites.sum() == 8 and (g0.nn[sites] == 1).all()
     rr, rp = synth.droplet_fields(shape, (12, 12, 12), 5.0, inside_r=False)
     p = lbm.Params(sigma=0.05, theta_deg=30.0, reaction_mode=1, xi=1.0, accel=(3.6e-5, 0, 0))
     op = _oparams(p, 0)

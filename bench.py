@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",
                     help="population storage of the headline run (the other is reported under variants)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--launch", default=None, metavar="M,D,N,P,F",
+                    help="fixed launch configuration (main, density and normal block sizes, programmatic launch "
+                         "0/1, fields 0-3) instead of the tuner; for profiling runs, whose serialised timing "
+                         "would mislead the tuner")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="T",
                     help="only time the adjoint variant over T steps and print its JSON (for profiling)")
     return ap.parse_args()
@@ -335,7 +339,12 @@ def run_native(args):
         L = lbm.Lattice(solid, params, bc_z=wl.bc_z, stream=stream.cuda_stream)
         info = L.info()
         L.step(warmup)
-        info["launch"] = L.tune()     # the library's launch-shape tuner, on the warmed-up state
+        if args.launch:
+            m, d, n, p, f = (int(v) for v in args.launch.split(","))
+            info["launch"] = dict(main=m, density=d, normal=n, pdl=p, fields=f)
+            L.set_launch(info["launch"])
+        else:
+            info["launch"] = L.tune()     # the library's launch-shape tuner, on the warmed-up state
         L.step(warmup)
         barrier()
         if clocks:

@@ -51,7 +51,7 @@ struct Batch {
   float4 *nsv = nullptr, *nrm = nullptr;
   float *rhoN = nullptr;
   long long nodes = 0;
-  uint32_t *bnd = nullptr;
+  uint32_t *bnd = nullptr, *bnd_link = nullptr;   // boundary-solid list and each entry's link word
   uint16_t *bnd_kid = nullptr;
   int n_bnd = 0;
   double *acc = nullptr, *acc_scratch = nullptr, *obs = nullptr;
@@ -154,7 +154,7 @@ void drop_graphs(Batch &b) {
 
 void free_all(Batch &b) {
   drop_graphs(b);
-  void *ptrs[] = {b.inst, b.kid, b.node, b.buf0, b.buf1, b.gidx, b.link, b.nsv, b.nrm, b.rhoN, b.bnd, b.bnd_kid,
+  void *ptrs[] = {b.inst, b.kid, b.node, b.buf0, b.buf1, b.gidx, b.link, b.nsv, b.nrm, b.rhoN, b.bnd, b.bnd_link, b.bnd_kid,
                   b.acc, b.acc_scratch, b.obs, b.err, b.dbg_H, b.dbg_delta, b.block_off};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
@@ -347,7 +347,7 @@ void launch_solids(const Batch &b, cudaStream_t st, bool colour) {
   const Inst &I = b.h[0].d;
   const unsigned g = (unsigned)((b.n_bnd + 127) / 128), g256 = (unsigned)((b.n_bnd + 255) / 256);
   const Inst *in = b.inst;
-  const uint32_t *bnd = b.bnd, *lk = b.link;
+  const uint32_t *bnd = b.bnd, *lk = b.bnd_link;
   const uint16_t *bk = b.bnd_kid;
   const int nb = b.n_bnd;
   if (colour) {
@@ -730,6 +730,7 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.block_off, hblock.size() * sizeof(int));
   if (b.n_bnd > 0) {
     rc = rc ? rc : dalloc(b, (void **)&b.bnd, (size_t)nbnd_tot * sizeof(uint32_t));
+    rc = rc ? rc : dalloc(b, (void **)&b.bnd_link, (size_t)nbnd_tot * sizeof(uint32_t));
     if (n > 1) rc = rc ? rc : dalloc(b, (void **)&b.bnd_kid, (size_t)nbnd_tot * sizeof(uint16_t));
   }
   if (rc) return rc;
@@ -740,7 +741,7 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
     int *gi = b.gidx + ih.d.gidx_off;
     k_layout_fill<<<(unsigned)(nblk[k + 1] - o), kLayoutBlock, 0, b.stream>>>(
         L, k, ih.d.slot_off, (int)bnd0[k], b.link + ih.d.node_off, cf + o, cb + o, gi, b.node, b.kid, b.bnd,
-        b.bnd_kid);
+        b.bnd_link, b.bnd_kid);
     k_layout_ghosts<<<(unsigned)((L.plane + 255) / 256), 256, 0, b.stream>>>(L, k, ih.d.ghost, gi, b.node, b.kid);
   }
   // every slot-map entry is a slot of the space or -1 (solid): the kernels index

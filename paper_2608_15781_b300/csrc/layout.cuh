@@ -101,12 +101,14 @@ __global__ void __launch_bounds__(1024) k_layout_scan(int nb, int *__restrict__ 
 }
 
 // Slots of instance k: gidx (lattice planes 0 .. nz - 1 at gi + plane), packed node
-// coordinates and instance of each fluid slot, boundary-solid list and its instances.
+// coordinates and instance of each fluid slot, boundary-solid list with each entry's
+// link word (read next to the entry by the solid kernels) and its instances.
 __global__ void __launch_bounds__(kLayoutBlock) k_layout_fill(Lattice L, int k, int slot_off, int bnd_off,
                                                               const uint32_t *__restrict__ link,
                                                               const int *__restrict__ cf, const int *__restrict__ cb,
                                                               int *__restrict__ gi, uint32_t *__restrict__ node,
                                                               uint16_t *__restrict__ kid, uint32_t *__restrict__ bnd,
+                                                              uint32_t *__restrict__ bnd_link,
                                                               uint16_t *__restrict__ bnd_kid) {
   const long long i = (long long)blockIdx.x * kLayoutBlock + threadIdx.x;
   const bool in = i < L.n;
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(kLayoutBlock) k_layout_fill(Lattice L, int k, 
     if (bs) {
       const int b = bnd_off + cb[blockIdx.x] + rb;
       bnd[b] = pk;
+      bnd_link[b] = lk;
       if (bnd_kid) bnd_kid[b] = (uint16_t)k;
     }
   }

@@ -806,6 +806,16 @@ def measure_adjoint(lbm, torch, stream, world, nsteps):
     torch.cuda.synchronize()
     t_f = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     t_b = max_over_ranks(e1.elapsed_time(e2), world, "cuda")
+    # the gradient's reproducibility: the same run from starts moved by 1e-6 (relative, random),
+    # i.e. how much of it is fixed by the objective rather than by rounding-level detail
+    rng = np.random.default_rng(1)
+    draws = []
+    for _ in range(2):
+        L.set_state((f0 * (1.0 + 1e-6 * rng.standard_normal(f0.shape))).astype(np.float32))
+        Jk = L.adjoint_forward(nsteps)
+        dthk, duk, _ = L.adjoint_backward()
+        draws.append({"objective": Jk, "dJ_du_in": duk,
+                      "dJ_dtheta_rel_change": float(np.linalg.norm(dthk - dth) / np.linalg.norm(dth))})
     K = int(np.ceil(np.sqrt(nsteps)))
     nstate = (nsteps + K - 1) // K + K + 3
     # reverse sweep per step and fluid node: recompute step (361 B) + adjoint step
@@ -818,6 +828,7 @@ def measure_adjoint(lbm, torch, stream, world, nsteps):
             "steps": nsteps, "checkpoint_every": K, "checkpoint_states": nstate,
             "ms_forward": round(t_f, 2), "ms_backward": round(t_b, 2), "objective": J,
             "dJ_du_in": du, "max_abs_dJ_dtheta_deg": float(np.abs(dth).max()),
+            "starts_moved_by_1e-6": draws,
             "reverse_effective_gbs": round(rev_bytes / (t_b * 1e-3) / 1e9, 1),
             "reverse_frac_of_peak": round(rev_bytes / (t_b * 1e-3) / 1e9 / peak, 4)}
 

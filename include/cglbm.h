@@ -125,8 +125,10 @@ typedef struct {
 
 /* Create a context: validates, copies the geometry to the device, builds the
  * static per-node data (bounce-back links, NN, r, wall flags, solid normals)
- * on the GPU, and sets the equilibrium start rho^r = 1, rho^p = 0, u = 0,
- * C = c_init.  *out is set only on success. */
+ * and the fluid-slot layout on the GPU (only three totals come back to the
+ * host), and sets the equilibrium start rho^r = 1, rho^p = 0, u = 0,
+ * C = c_init.  LBM_EINVAL also for a mask without fluid nodes.  *out is set
+ * only on success. */
 int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out);
 
 /* Advance nsteps >= 0 time steps, asynchronously on the context's stream.

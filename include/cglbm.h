@@ -127,8 +127,8 @@ typedef struct {
  * static per-node data (bounce-back links, NN, r, wall flags, solid normals)
  * and the fluid-slot layout on the GPU (only three totals come back to the
  * host), and sets the equilibrium start rho^r = 1, rho^p = 0, u = 0,
- * C = c_init.  LBM_EINVAL also for a mask without fluid nodes.  *out is set
- * only on success. */
+ * C = c_init.  LBM_EINVAL also for a mask without fluid nodes (checked on
+ * the host before any device call).  *out is set only on success. */
 int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out);
 
 /* Advance nsteps >= 0 time steps, asynchronously on the context's stream.

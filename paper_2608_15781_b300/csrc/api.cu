@@ -1453,7 +1453,10 @@ const char *lbm_strerror(int code) {
 
 int lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out) {
   if (!out || check_geometry(geom) || check_params(params)) return LBM_EINVAL;
-  lbm_ctx *c = new (std::nothrow) lbm_ctx();   // a mask without fluid is rejected by the layout pass
+  // a mask without a fluid node (byte 0) is rejected before any device call; memchr stops at the first one
+  const size_t n = (size_t)geom->nx * geom->ny * geom->nz;
+  if (!std::memchr(geom->solid, 0, n)) return LBM_EINVAL;
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ENOMEM;
   const int rc = batch_create(c->b, 1, geom, params, params->cuda_stream);
   if (rc) {

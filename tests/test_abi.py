@@ -48,8 +48,9 @@ def test_invalid_arguments_rejected_on_host(lib):
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_create(solid, bad)
         assert e.value.code == lbm.LBM_EINVAL
-    with pytest.raises(lbm.LbmError):
+    with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(np.ones((3, 3, 3), np.uint8), lbm.Params())      # no fluid node
+    assert e.value.code == lbm.LBM_EINVAL
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create(np.zeros((1, 4, 4), np.uint8), lbm.Params(), bc_z=1)   # column needs nz >= 2
     with pytest.raises(lbm.LbmError):

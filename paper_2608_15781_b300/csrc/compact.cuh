@@ -63,25 +63,48 @@ __device__ __forceinline__ void unpack(uint32_t pk, int &x, int &y, int &z) {
 // reference value subtracted before FP16 storage of population p
 __device__ __forceinline__ float pop_ref(int p) { return p < Q ? W[p] : (p < 2 * Q ? 0.f : W7[p - 2 * Q]); }
 
+// Population storage.  Population p of slot t: ld / st / st_r address it by
+// (p, t) with ns the population stride; ld2 / st2_r move f^r_i and f^p_i of one
+// slot together (i < Q), the pair the pull and the main kernel always access
+// together.  ld2 reads the pair of direction i and adds the references of
+// direction iref (the same value: the weights are even in c, so a bounced pair
+// read from the opposite direction keeps the compile-time reference).
 template <typename T>
 struct Store;
 template <>
 struct Store<float> {
-  static __device__ __forceinline__ float ld(const float *__restrict__ f, unsigned idx, int) { return f[idx]; }
-  static __device__ __forceinline__ void st(float *__restrict__ f, unsigned idx, int, float v) { f[idx] = v; }
-  static __device__ __forceinline__ void st_r(float *__restrict__ f, unsigned idx, int, float v, uint32_t) {
-    f[idx] = v;
+  // FP32: structure of arrays, population p of slot t at p * ns + t
+  static __device__ __forceinline__ float ld(const float *__restrict__ f, unsigned ns, unsigned p, unsigned t) {
+    return f[p * ns + t];
+  }
+  static __device__ __forceinline__ void st(float *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v) {
+    f[p * ns + t] = v;
+  }
+  static __device__ __forceinline__ void st_r(float *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v,
+                                              uint32_t) {
+    f[p * ns + t] = v;
+  }
+  static __device__ __forceinline__ void ld2(const float *__restrict__ f, unsigned ns, unsigned i, unsigned t, int,
+                                             float &a, float &b) {
+    a = f[i * ns + t];
+    b = f[(i + Q) * ns + t];
+  }
+  static __device__ __forceinline__ void st2_r(float *__restrict__ f, unsigned ns, unsigned i, unsigned t, float a,
+                                               float b, uint32_t, uint32_t) {
+    f[i * ns + t] = a;
+    f[(i + Q) * ns + t] = b;
   }
 };
 // FP32 -> FP16 with stochastic rounding: round away from zero with probability equal
 // to the discarded fraction of an FP16 spacing, so that per-step changes smaller than
 // half a spacing (which round-to-nearest drops every step) survive in expectation.
-// The random bits come from a hash of the value's bits and the storage index, so the
-// rounding is deterministic and reproducible.  In the FP16 normal range the 13
-// discarded mantissa bits receive 13 random bits before truncation; below it (values
-// under 6.1e-5, spacing 6e-8) the rounding leans toward zero by less than one spacing.
-// Non-finite values get no random bits: added to a NaN pattern such as 0x7fffffff
-// they would carry into the sign bit and store a NaN as -0.
+// The random bits come from a hash of the value's bits and the population's logical
+// index p * ns + t, so the rounding is deterministic and reproducible.  In the FP16
+// normal range the 13 discarded mantissa bits receive 13 random bits before
+// truncation; below it (values under 6.1e-5, spacing 6e-8) the rounding leans toward
+// zero by less than one spacing.  Non-finite values get no random bits: added to a
+// NaN pattern such as 0x7fffffff they would carry into the sign bit and store a NaN
+// as -0.
 __device__ __forceinline__ uint32_t round_bits(uint32_t bits, unsigned idx) {
   uint32_t h = (bits ^ idx) * 0x9E3779B9u;
   h ^= h >> 15;
@@ -112,18 +135,45 @@ __device__ __forceinline__ uint32_t pop_random(uint32_t seed, int p) {
   return seed * ((0x9E3779B9u ^ ((uint32_t)p * 0x632BE5ABu)) | 1u);
 }
 
+// two FP32 values -> one 32-bit word of two FP16 halves, each rounded toward zero
+// (lo at the lower address)
+__device__ __forceinline__ uint32_t pack_half2_rz(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 template <>
 struct Store<__half> {
-  static __device__ __forceinline__ float ld(const __half *__restrict__ f, unsigned idx, int p) {
-    return __half2float(f[idx]) + pop_ref(p);
+  // FP16 deviations from the reference equilibria: f^r_i - w_i, f^p_i, g_j - w_j.
+  // f^r_i and f^p_i of slot t share one 32-bit word (halves 2 (i ns + t) and
+  // 2 (i ns + t) + 1); g_j follows at 2 Q ns + j ns + t.
+  static __device__ __forceinline__ unsigned hidx(unsigned ns, unsigned p, unsigned t) {
+    return p < (unsigned)Q ? 2u * (p * ns + t) : (p < 2u * Q ? 2u * ((p - Q) * ns + t) + 1u : p * ns + t);
   }
-  static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned idx, int p, float v) {
-    f[idx] = half_stochastic(v - pop_ref(p), idx);
+  static __device__ __forceinline__ float ld(const __half *__restrict__ f, unsigned ns, unsigned p, unsigned t) {
+    return __half2float(f[hidx(ns, p, t)]) + pop_ref(p);
+  }
+  static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v) {
+    f[hidx(ns, p, t)] = half_stochastic(v - pop_ref(p), p * ns + t);
   }
   // the same rounding with the random word r supplied by the caller (top 13 bits
   // used); the caller passes r = 0 for a node with a non-finite value (node_seed)
-  static __device__ __forceinline__ void st_r(__half *__restrict__ f, unsigned idx, int p, float v, uint32_t r) {
-    f[idx] = __float2half_rz(__uint_as_float(__float_as_uint(v - pop_ref(p)) + (r >> 19)));
+  static __device__ __forceinline__ void st_r(__half *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v,
+                                              uint32_t r) {
+    f[hidx(ns, p, t)] = __float2half_rz(__uint_as_float(__float_as_uint(v - pop_ref(p)) + (r >> 19)));
+  }
+  static __device__ __forceinline__ void ld2(const __half *__restrict__ f, unsigned ns, unsigned i, unsigned t,
+                                             int iref, float &a, float &b) {
+    const float2 v = __half22float2(reinterpret_cast<const __half2 *>(f)[i * ns + t]);
+    a = v.x + W[iref];
+    b = v.y + 0.f;   // the reference of f^p is 0 (the addition maps -0 to +0, as ld does)
+  }
+  static __device__ __forceinline__ void st2_r(__half *__restrict__ f, unsigned ns, unsigned i, unsigned t, float a,
+                                               float b, uint32_t ra, uint32_t rb) {
+    const float ua = __uint_as_float(__float_as_uint(a - W[i]) + (ra >> 19));
+    const float ub = __uint_as_float(__float_as_uint(b) + (rb >> 19));
+    reinterpret_cast<uint32_t *>(f)[i * ns + t] = pack_half2_rz(ua, ub);
   }
 };
 
@@ -225,8 +275,7 @@ __device__ __forceinline__ void pull_compact(int ns_, const StepParams &P, const
     const unsigned s = bb ? t : (unsigned)src[i];
     const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
     // the reference of population OPP[i] equals that of i (w is even in c)
-    fr[i] = Store<T>::ld(fin, pr * ns + s, i);
-    fp[i] = Store<T>::ld(fin, (pr + Q) * ns + s, Q + i);
+    Store<T>::ld2(fin, ns, pr, s, i, fr[i], fp[i]);
   }
   if (P.reaction_mode == 0) {
 #pragma unroll
@@ -235,7 +284,7 @@ __device__ __forceinline__ void pull_compact(int ns_, const StepParams &P, const
       const bool bb = src[d] < 0;
       const unsigned s = bb ? t : (unsigned)src[d];
       const unsigned pj = bb ? (unsigned)GOPP[j] : (unsigned)j;
-      g[j] = Store<T>::ld(fin, (2 * Q + pj) * ns + s, 2 * Q + j);
+      g[j] = Store<T>::ld(fin, ns, 2 * Q + pj, s);
     }
   }
 }
@@ -272,8 +321,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, cons
     const bool bb = si < 0;
     const unsigned s = bb ? t : (unsigned)si;
     const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
-    rr += Store<T>::ld(f, pr * ns + s, i);
-    rp += Store<T>::ld(f, (pr + Q) * ns + s, Q + i);
+    float a, b;
+    Store<T>::ld2(f, ns, pr, s, i, a, b);
+    rr += a;
+    rp += b;
   }
   rhoN[(BATCH ? I.node_off : 0) + nidx(I.L, x, y, z)] = (rr - rp) / (rr + rp);
 }
@@ -638,10 +689,10 @@ __device__ __forceinline__ void write_outlet_ghost_c(int ns_, T *__restrict__ f,
   for (int i = 0; i < Q; ++i) {
     if (CZ[i] != -1) continue;
     const float corr = feq19(i, rho_out - rho, vx, vy, vz, vv);
-    Store<T>::st(f, (unsigned)i * ns + gs, i, fr[i] + psi * corr);
-    Store<T>::st(f, (unsigned)(Q + i) * ns + gs, Q + i, fp[i] + (1.0f - psi) * corr);
+    Store<T>::st(f, ns, i, gs, fr[i] + psi * corr);
+    Store<T>::st(f, ns, Q + i, gs, fp[i] + (1.0f - psi) * corr);
   }
-  Store<T>::st(f, (unsigned)(2 * Q + 5) * ns + gs, 2 * Q + 5, g5);
+  Store<T>::st(f, ns, 2 * Q + 5, gs, g5);
 }
 
 // a1, a2, a6 - a10 over the fluid slots; stores are coalesced and whole-sector.
@@ -691,17 +742,16 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     const uint32_t seed = node_seed(fr[Q - 1] + fp[Q - 1] + (I.P.reaction_mode == 0 ? g[Q7 - 1] : 0.f), t);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      Store<T>::st_r(fout, (unsigned)i * ns + t, i, fr[i], pop_random(seed, i));
-      Store<T>::st_r(fout, (unsigned)(Q + i) * ns + t, Q + i, fp[i], pop_random(seed, Q + i));
+      Store<T>::st2_r(fout, ns, i, t, fr[i], fp[i], pop_random(seed, i), pop_random(seed, Q + i));
     }
     float g5;
     if (I.P.reaction_mode == 0) {
 #pragma unroll
       for (int j = 0; j < Q7; ++j)
-        Store<T>::st_r(fout, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j, g[j], pop_random(seed, 2 * Q + j));
+        Store<T>::st_r(fout, ns, 2 * Q + j, t, g[j], pop_random(seed, 2 * Q + j));
       g5 = g[5];
     } else {
-      g5 = Store<T>::ld(fin, (unsigned)(2 * Q + 5) * ns + t, 2 * Q + 5);
+      g5 = Store<T>::ld(fin, ns, 2 * Q + 5, t);
     }
     if (I.L.bc_z == 1 && z == I.L.nz - 1) {
       const unsigned gs = (unsigned)(I.ghost + I.L.plane) + (unsigned)(y * I.L.nx + x);
@@ -735,17 +785,17 @@ __global__ void k_init_c(Inst I, int ns_, const uint32_t *__restrict__ node, con
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const float a = feq19(i, rr, ux, uy, uz, uu), b = feq19(i, rp, ux, uy, uz, uu);
-    Store<T>::st(fa, (unsigned)i * ns + t, i, a);
-    Store<T>::st(fb, (unsigned)i * ns + t, i, a);
-    Store<T>::st(fa, (unsigned)(Q + i) * ns + t, Q + i, b);
-    Store<T>::st(fb, (unsigned)(Q + i) * ns + t, Q + i, b);
+    Store<T>::st(fa, ns, i, t, a);
+    Store<T>::st(fb, ns, i, t, a);
+    Store<T>::st(fa, ns, Q + i, t, b);
+    Store<T>::st(fb, ns, Q + i, t, b);
   }
 #pragma unroll
   for (int j = 0; j < Q7; ++j) {
     const int d = GDIR[j];
     const float gv = W7[j] * cc * (1.0f + 4.0f * (CX[d] * ux + CY[d] * uy + CZ[d] * uz));
-    Store<T>::st(fa, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j, gv);
-    Store<T>::st(fb, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j, gv);
+    Store<T>::st(fa, ns, 2 * Q + j, t, gv);
+    Store<T>::st(fb, ns, 2 * Q + j, t, gv);
   }
 }
 
@@ -764,37 +814,36 @@ __global__ void k_ghost_init_c(Inst I, int ns_, const int *__restrict__ gidx, fl
   const float uu = u_in * u_in;
 #pragma unroll
   for (int p = 0; p < NPOP; ++p) {
-    Store<T>::st(fa, (unsigned)p * ns + gin, p, 0.f);
-    Store<T>::st(fb, (unsigned)p * ns + gin, p, 0.f);
-    Store<T>::st(fa, (unsigned)p * ns + gout, p, 0.f);
-    Store<T>::st(fb, (unsigned)p * ns + gout, p, 0.f);
+    Store<T>::st(fa, ns, p, gin, 0.f);
+    Store<T>::st(fb, ns, p, gin, 0.f);
+    Store<T>::st(fa, ns, p, gout, 0.f);
+    Store<T>::st(fb, ns, p, gout, 0.f);
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (CZ[i] != 1) continue;
     const float v = feq19(i, 1.0f, 0.f, 0.f, u_in, uu);
-    Store<T>::st(fa, (unsigned)i * ns + gin, i, v);
-    Store<T>::st(fb, (unsigned)i * ns + gin, i, v);
+    Store<T>::st(fa, ns, i, gin, v);
+    Store<T>::st(fb, ns, i, gin, v);
   }
   const float g4 = W7[4] * c_in * (1.0f + 4.0f * u_in);
-  Store<T>::st(fa, (unsigned)(2 * Q + 4) * ns + gin, 2 * Q + 4, g4);
-  Store<T>::st(fb, (unsigned)(2 * Q + 4) * ns + gin, 2 * Q + 4, g4);
+  Store<T>::st(fa, ns, 2 * Q + 4, gin, g4);
+  Store<T>::st(fb, ns, 2 * Q + 4, gin, g4);
   const int s = gidx[I.gidx_off + (long long)L.nz * L.plane + (long long)y * L.nx + x];   // z = nz - 1
   if (s < 0) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (CZ[i] != -1) continue;
-      Store<T>::st(fa, (unsigned)i * ns + gout, i, W[i] * rho_out);
-      Store<T>::st(fb, (unsigned)i * ns + gout, i, W[i] * rho_out);
+      Store<T>::st(fa, ns, i, gout, W[i] * rho_out);
+      Store<T>::st(fb, ns, i, gout, W[i] * rho_out);
     }
   } else {
     float fr[Q], fp[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      fr[i] = Store<T>::ld(fa, (unsigned)i * ns + (unsigned)s, i);
-      fp[i] = Store<T>::ld(fa, (unsigned)(Q + i) * ns + (unsigned)s, Q + i);
+      Store<T>::ld2(fa, ns, i, (unsigned)s, i, fr[i], fp[i]);
     }
-    const float g5 = Store<T>::ld(fa, (unsigned)(2 * Q + 5) * ns + (unsigned)s, 2 * Q + 5);
+    const float g5 = Store<T>::ld(fa, ns, 2 * Q + 5, (unsigned)s);
     write_outlet_ghost_c<T>(ns_, fa, gout, fr, fp, g5, rho_out);
   }
 }
@@ -817,14 +866,14 @@ __global__ void k_observables_c(Slots S, const __grid_constant__ Inst single, co
     float rr = 0.f, rp = 0.f, cc = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float a = Store<T>::ld(f, (unsigned)i * ns + t, i);
-      const float b = Store<T>::ld(f, (unsigned)(Q + i) * ns + t, Q + i);
+      float a, b;
+      Store<T>::ld2(f, ns, i, t, i, a, b);
       rr += a;
       rp += b;
       if (CZ[i]) jz += CZ[i] * (a + b);
     }
 #pragma unroll
-    for (int j = 0; j < Q7; ++j) cc += Store<T>::ld(f, (unsigned)(2 * Q + j) * ns + t, 2 * Q + j);
+    for (int j = 0; j < Q7; ++j) cc += Store<T>::ld(f, ns, 2 * Q + j, t);
     const float rho = rr + rp;
     v[0] = rr;
     v[1] = rp;

@@ -171,7 +171,7 @@ __global__ void k_slots_to_dense(Inst I, int ns_, const uint32_t *__restrict__ n
   unpack(node[t], x, y, z);
   const long long nd = nidx(I.L, x, y, z);
 #pragma unroll
-  for (int p = 0; p < NPOP; ++p) dst[(long long)p * I.L.n + nd] = Store<T>::ld(src, (unsigned)p * (unsigned)ns_ + t, p);
+  for (int p = 0; p < NPOP; ++p) dst[(long long)p * I.L.n + nd] = Store<T>::ld(src, (unsigned)ns_, p, t);
 }
 template <typename T>
 __global__ void k_dense_to_slots(Inst I, int ns_, const uint32_t *__restrict__ node, const float *__restrict__ src,
@@ -185,8 +185,8 @@ __global__ void k_dense_to_slots(Inst I, int ns_, const uint32_t *__restrict__ n
 #pragma unroll
   for (int p = 0; p < NPOP; ++p) {
     const float v = src[(long long)p * I.L.n + nd];
-    Store<T>::st(a, (unsigned)p * (unsigned)ns_ + t, p, v);
-    Store<T>::st(b, (unsigned)p * (unsigned)ns_ + t, p, v);
+    Store<T>::st(a, (unsigned)ns_, p, t, v);
+    Store<T>::st(b, (unsigned)ns_, p, t, v);
   }
 }
 

@@ -374,11 +374,13 @@ __global__ void k_adj_seed(Slots S, const __grid_constant__ Inst I, const float 
   }
   float rho = 0.f, jz = 0.f, cc = 0.f;
   for (int i = 0; i < Q; ++i) {
-    const float m = f[(unsigned)i * ns + t] + f[(unsigned)(Q + i) * ns + t];
+    float fr, fp;
+    Store<float>::ld2(f, ns, i, t, i, fr, fp);   // the forward state, in the slot layout
+    const float m = fr + fp;
     rho += m;
     jz += CZ[i] * m;
   }
-  for (int j = 0; j < Q7; ++j) cc += f[(unsigned)(2 * Q + j) * ns + t];
+  for (int j = 0; j < Q7; ++j) cc += Store<float>::ld(f, ns, 2 * Q + j, t);
   const float inv = 1.0f / rho;
   for (int i = 0; i < Q; ++i) {
     const float v = a * cc * (CZ[i] * inv - jz * inv * inv);
@@ -748,8 +750,7 @@ __global__ void k_adj_ghost0(Slots S, const __grid_constant__ Inst I, const floa
   const unsigned gs = (unsigned)(I.ghost + I.L.plane) + (unsigned)(y * I.L.nx + x);
   float fr[Q], fp[Q], gr[Q], gp[Q], lr[Q], lp[Q];
   for (int i = 0; i < Q; ++i) {
-    fr[i] = f0[(unsigned)i * ns + t];
-    fp[i] = f0[(unsigned)(Q + i) * ns + t];
+    Store<float>::ld2(f0, ns, i, t, i, fr[i], fp[i]);   // the start state, in the slot layout
     gr[i] = CZ[i] == -1 ? lam[(unsigned)i * ns + gs] : 0.f;
     gp[i] = CZ[i] == -1 ? lam[(unsigned)(Q + i) * ns + gs] : 0.f;
     lr[i] = lam[(unsigned)i * ns + t];

@@ -818,9 +818,10 @@ int init_fields(Batch &b, int k, const float *rho_r, const float *rho_p, const f
   return rc;
 }
 
-// slot-space populations src (storage type T) of instance k -> host [45][n], zero at solids
-// (scattered into a dense device array, then one copy)
-template <typename T>
+// slot-space populations src (storage type T, the state's slot layout, or with SOA an
+// adjoint array in population-major order) of instance k -> host [45][n], zero at
+// solids (scattered into a dense device array, then one copy)
+template <typename T, bool SOA = false>
 int slots_to_host(Batch &b, int k, const T *src, float *dst, size_t bytes) {
   const InstHost &ih = b.h[k];
   float *d = nullptr;
@@ -830,7 +831,10 @@ int slots_to_host(Batch &b, int k, const T *src, float *dst, size_t bytes) {
   }
   cudaError_t e = cudaMemsetAsync(d, 0, bytes, b.stream);   // solid nodes hold no populations
   if (e == cudaSuccess) {
-    k_slots_to_dense<T><<<(unsigned)((ih.d.nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, b.node, src, d);
+    if constexpr (SOA)
+      k_soa_to_dense<<<(unsigned)((ih.d.nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, b.node, src, d);
+    else
+      k_slots_to_dense<T><<<(unsigned)((ih.d.nf + 255) / 256), 256, 0, b.stream>>>(ih.d, b.ns, b.node, src, d);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, b.stream);
@@ -1324,7 +1328,7 @@ int adjoint_backward(Batch &b, double seed, double *dtheta, double *du_in, float
   if (dstate) {
     k_adj_ghost0<<<(unsigned)((S.nslots + 255) / 256), 256, 0, b.stream>>>(S, ih.d, a.cp[0], lam);
     CK(cudaGetLastError());
-    const int rc = slots_to_host<float>(b, 0, lam, dstate, state_bytes);
+    const int rc = slots_to_host<float, true>(b, 0, lam, dstate, state_bytes);   // adjoint order
     if (rc) return rc;
   }
   return LBM_OK;

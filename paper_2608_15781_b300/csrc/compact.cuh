@@ -71,28 +71,35 @@ __device__ __forceinline__ float pop_ref(int p) { return p < Q ? W[p] : (p < 2 *
 // read from the opposite direction keeps the compile-time reference).
 template <typename T>
 struct Store;
+// Slot layout shared by both storage types: f^r_i and f^p_i of slot t are
+// adjacent (elements 2 (i ns + t) and 2 (i ns + t) + 1), so the pull, the density
+// pass and the main kernel move the pair with one access; g_j follows at
+// 2 Q ns + j ns + t.  (The adjoint's own arrays keep population-major order.)
+__device__ __forceinline__ unsigned pop_index(unsigned ns, unsigned p, unsigned t) {
+  return p < (unsigned)Q ? 2u * (p * ns + t) : (p < 2u * Q ? 2u * ((p - Q) * ns + t) + 1u : p * ns + t);
+}
+
 template <>
 struct Store<float> {
-  // FP32: structure of arrays, population p of slot t at p * ns + t
   static __device__ __forceinline__ float ld(const float *__restrict__ f, unsigned ns, unsigned p, unsigned t) {
-    return f[p * ns + t];
+    return f[pop_index(ns, p, t)];
   }
   static __device__ __forceinline__ void st(float *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v) {
-    f[p * ns + t] = v;
+    f[pop_index(ns, p, t)] = v;
   }
   static __device__ __forceinline__ void st_r(float *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v,
                                               uint32_t) {
-    f[p * ns + t] = v;
+    f[pop_index(ns, p, t)] = v;
   }
   static __device__ __forceinline__ void ld2(const float *__restrict__ f, unsigned ns, unsigned i, unsigned t, int,
                                              float &a, float &b) {
-    a = f[i * ns + t];
-    b = f[(i + Q) * ns + t];
+    const float2 v = reinterpret_cast<const float2 *>(f)[i * ns + t];
+    a = v.x;
+    b = v.y;
   }
   static __device__ __forceinline__ void st2_r(float *__restrict__ f, unsigned ns, unsigned i, unsigned t, float a,
                                                float b, uint32_t, uint32_t) {
-    f[i * ns + t] = a;
-    f[(i + Q) * ns + t] = b;
+    reinterpret_cast<float2 *>(f)[i * ns + t] = make_float2(a, b);
   }
 };
 // FP32 -> FP16 with stochastic rounding: round away from zero with probability equal
@@ -145,12 +152,9 @@ __device__ __forceinline__ uint32_t pack_half2_rz(float lo, float hi) {
 
 template <>
 struct Store<__half> {
-  // FP16 deviations from the reference equilibria: f^r_i - w_i, f^p_i, g_j - w_j.
-  // f^r_i and f^p_i of slot t share one 32-bit word (halves 2 (i ns + t) and
-  // 2 (i ns + t) + 1); g_j follows at 2 Q ns + j ns + t.
-  static __device__ __forceinline__ unsigned hidx(unsigned ns, unsigned p, unsigned t) {
-    return p < (unsigned)Q ? 2u * (p * ns + t) : (p < 2u * Q ? 2u * ((p - Q) * ns + t) + 1u : p * ns + t);
-  }
+  // FP16 deviations from the reference equilibria: f^r_i - w_i, f^p_i, g_j - w_j, in
+  // the slot layout above (the f^r_i / f^p_i pair of a slot in one 32-bit word).
+  static __device__ __forceinline__ unsigned hidx(unsigned ns, unsigned p, unsigned t) { return pop_index(ns, p, t); }
   static __device__ __forceinline__ float ld(const __half *__restrict__ f, unsigned ns, unsigned p, unsigned t) {
     return __half2float(f[hidx(ns, p, t)]) + pop_ref(p);
   }

@@ -173,6 +173,18 @@ __global__ void k_slots_to_dense(Inst I, int ns_, const uint32_t *__restrict__ n
 #pragma unroll
   for (int p = 0; p < NPOP; ++p) dst[(long long)p * I.L.n + nd] = Store<T>::ld(src, (unsigned)ns_, p, t);
 }
+// an adjoint array (population-major p * ns + t, not the state's slot layout) -> dense
+__global__ void k_soa_to_dense(Inst I, int ns_, const uint32_t *__restrict__ node, const float *__restrict__ src,
+                               float *__restrict__ dst) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= I.nf) return;
+  const unsigned t = (unsigned)(I.slot_off + l);
+  int x, y, z;
+  unpack(node[t], x, y, z);
+  const long long nd = nidx(I.L, x, y, z);
+#pragma unroll
+  for (int p = 0; p < NPOP; ++p) dst[(long long)p * I.L.n + nd] = src[(unsigned)p * (unsigned)ns_ + t];
+}
 template <typename T>
 __global__ void k_dense_to_slots(Inst I, int ns_, const uint32_t *__restrict__ node, const float *__restrict__ src,
                                  T *__restrict__ a, T *__restrict__ b) {

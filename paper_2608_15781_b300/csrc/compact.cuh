@@ -307,7 +307,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, cons
                                                      const T *__restrict__ f, const int *__restrict__ gidx,
                                                      float *__restrict__ rhoN) {
   pdl_begin();
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  // the blocks walk the slots from the end: the first ones read what the main kernel
+  // of the previous step wrote last, which is still in L2 (67.5 -> 65.1 us on the
+  // 128x128x256 column)
+  const unsigned t = (gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= (unsigned)S.nslots) return;
   const uint32_t pk = S.node[t];
   if (pk == kNoNode) return;

@@ -56,6 +56,7 @@ struct Batch {
   int n_bnd = 0;
   double *acc = nullptr, *acc_scratch = nullptr, *obs = nullptr;
   int *err = nullptr;
+  uint32_t *rstep = nullptr;          // step counter of the FP16 rounding bits (two entries, by step parity)
   float *dbg_H = nullptr, *dbg_delta = nullptr;
   bool debug = false;
   size_t device_bytes = 0;
@@ -155,7 +156,7 @@ void drop_graphs(Batch &b) {
 void free_all(Batch &b) {
   drop_graphs(b);
   void *ptrs[] = {b.inst, b.kid, b.node, b.buf0, b.buf1, b.gidx, b.link, b.nsv, b.nrm, b.rhoN, b.bnd, b.bnd_link, b.bnd_kid,
-                  b.acc, b.acc_scratch, b.obs, b.err, b.dbg_H, b.dbg_delta, b.block_off};
+                  b.acc, b.acc_scratch, b.obs, b.err, b.rstep, b.dbg_H, b.dbg_delta, b.block_off};
   for (void *p : ptrs) cudaFree(p);
   for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
   b.ev.clear();
@@ -324,15 +325,15 @@ void launch_main_t(const Batch &b, cudaStream_t st, const void *fin, void *fout,
   switch (b.main_block) {
     case 64:
       launch_step_kernel(b.pdl, k_main_c<T, 64, BT>, (S.nslots + 63) / 64, 64, st, S, I, n, fi, fo, gi, lk, nrm, acc,
-                         slot, dh, dd);
+                         slot, b.rstep, dh, dd);
       break;
     case 256:
       launch_step_kernel(b.pdl, k_main_c<T, 256, BT>, (S.nslots + 255) / 256, 256, st, S, I, n, fi, fo, gi, lk, nrm,
-                         acc, slot, dh, dd);
+                         acc, slot, b.rstep, dh, dd);
       break;
     default:
       launch_step_kernel(b.pdl, k_main_c<T, 128, BT>, (S.nslots + 127) / 128, 128, st, S, I, n, fi, fo, gi, lk, nrm,
-                         acc, slot, dh, dd);
+                         acc, slot, b.rstep, dh, dd);
   }
 }
 template <typename T>
@@ -611,10 +612,12 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   rc = rc ? rc : dalloc(b, (void **)&b.acc_scratch, 4 * sizeof(double) * n);
   rc = rc ? rc : dalloc(b, (void **)&b.obs, 8 * sizeof(double) * n);
   rc = rc ? rc : dalloc(b, (void **)&b.err, sizeof(int));
+  rc = rc ? rc : dalloc(b, (void **)&b.rstep, 2 * sizeof(uint32_t));
   if (rc) return rc;
   CK(cudaMemsetAsync(b.rhoN, 0, nodes * sizeof(float), b.stream));
   CK(cudaMemsetAsync(b.nrm, 0, nodes * sizeof(float4), b.stream));
   CK(cudaMemsetAsync(b.err, 0, sizeof(int), b.stream));
+  CK(cudaMemsetAsync(b.rstep, 0, 2 * sizeof(uint32_t), b.stream));
   {
     // geometry kernels, one instance at a time (one-time set-up)
     uint8_t *d_solid = nullptr, *d_react = nullptr;

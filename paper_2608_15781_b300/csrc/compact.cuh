@@ -21,7 +21,7 @@
 //
 // Storage type T: float (FP32) or __half (FP16 deviations from fixed reference
 // equilibria: f^r_i - w_i, f^p_i, g_j - w_j, i.e. reactant liquid at rest with
-// C = 1; all arithmetic in FP32).
+// C = 1, scaled by 2^12; all arithmetic in FP32).
 #pragma once
 #include <cuda_fp16.h>
 
@@ -60,8 +60,20 @@ __device__ __forceinline__ void unpack(uint32_t pk, int &x, int &y, int &z) {
   z = (int)((pk >> 20) & 2047u);
 }
 
-// reference value subtracted before FP16 storage of population p
-__device__ __forceinline__ float pop_ref(int p) { return p < Q ? W[p] : (p < 2 * Q ? 0.f : W7[p - 2 * Q]); }
+// Reference values subtracted before FP16 storage: the weights w_i of f^r_i on a
+// 2^-20 grid, summing to exactly 1 (6 x 58254 + 12 x 29127 + 349528 = 2^20), 0 for
+// f^p_i and w_j (exact binary fractions) for g_j.  A reference is only an offset:
+// any value near w_i serves, and the stored deviation is taken against the same
+// one.  On the grid every partial sum of the references is exact in FP32, so the
+// rounding of the sum of a node's 19 pulled f^r_i comes from the deviations alone.
+// With the FP32-rounded w_i (whose low bits are the same at every node) that
+// rounding leans one way whenever the deviations are coarse, as FP16 deviations
+// are: +4e-8 per node and step, a steady gain of red mass (0.03 % over 5000 steps
+// of the 64^3 crop of the 256^3 precision box).
+constexpr float WR1 = 58254.0f / 1048576.0f, WR2 = 29127.0f / 1048576.0f, WR0 = 349528.0f / 1048576.0f;
+__device__ constexpr float WREF[Q] = {WR1, WR1, WR1, WR1, WR1, WR1, WR2, WR2, WR2, WR2,
+                                      WR2, WR2, WR2, WR2, WR2, WR2, WR2, WR2, WR0};
+__device__ __forceinline__ float pop_ref(int p) { return p < Q ? WREF[p] : (p < 2 * Q ? 0.f : W7[p - 2 * Q]); }
 
 // Population storage.  Population p of slot t: ld / st / st_r address it by
 // (p, t) with ns the population stride; ld2 / st2_r move f^r_i and f^p_i of one
@@ -105,11 +117,18 @@ struct Store<float> {
 // FP32 -> FP16 with stochastic rounding: round away from zero with probability equal
 // to the discarded fraction of an FP16 spacing, so that per-step changes smaller than
 // half a spacing (which round-to-nearest drops every step) survive in expectation.
-// The random bits come from a hash of the value's bits and the population's logical
-// index p * ns + t, so the rounding is deterministic and reproducible.  In the FP16
-// normal range the 13 discarded mantissa bits receive 13 random bits before
-// truncation; below it (values under 6.1e-5, spacing 6e-8) the rounding leans toward
-// zero by less than one spacing.  Non-finite values get no random bits: added to a
+// In the FP16 normal range the 13 discarded mantissa bits receive 13 random bits
+// before truncation; below it the rounding leans toward zero by less than one
+// spacing, so the stored deviations are scaled by 2^12 first (kHalfScale): the normal
+// range then starts at 1.5e-8 instead of 6.1e-5, and deviations up to 16 in
+// magnitude are representable (a larger one saturates; populations of a run near
+// rho = 1 stay far below).  The rounding is unbiased only if the random bits are
+// independent of the value's discarded bits, also from one step to the next: a node
+// whose value repeats must not round the same way every step.  The per-step stores
+// of the main kernel therefore draw their bits from the slot and a step counter
+// (node_seed); the one-time writes (start, set_state, ghost set-up) hash the value's
+// bits and the population's logical index p * ns + t (round_bits).  Both are
+// deterministic and reproducible.  Non-finite values get no random bits: added to a
 // NaN pattern such as 0x7fffffff they would carry into the sign bit and store a NaN
 // as -0.
 __device__ __forceinline__ uint32_t round_bits(uint32_t bits, unsigned idx) {
@@ -119,20 +138,25 @@ __device__ __forceinline__ uint32_t round_bits(uint32_t bits, unsigned idx) {
   h ^= h >> 12;
   return (bits & 0x7f800000u) == 0x7f800000u ? 0u : h;
 }
+constexpr float kHalfScale = 4096.f, kHalfUnscale = 1.f / 4096.f;
 __device__ __forceinline__ __half half_stochastic(float x, unsigned idx) {
   const uint32_t bits = __float_as_uint(x);
   return __float2half_rz(__uint_as_float(bits + (round_bits(bits, idx) >> 19)));
 }
 
-// The main kernel stores 45 values per node: it hashes once per node (node_seed)
-// and gives population p the top 13 bits of seed * K_p, K_p an odd constant per
-// population -- one multiply per store instead of a hash per store.  v is the
-// node's post-collision rest population, a function of every pulled value
-// (through rho and C), so it is non-finite whenever any stored value is: the seed
-// is then 0 and no random bits are added, which keeps a NaN a NaN (added to a NaN
-// pattern such as 0x7fffffff they would carry into the sign bit).
-__device__ __forceinline__ uint32_t node_seed(float v, unsigned t) {
-  uint32_t h = (__float_as_uint(v) ^ (t * 0x85EBCA6Bu)) * 0x9E3779B9u;
+// The main kernel stores 45 values per node (and its outlet ghost's): it hashes
+// the slot t and the step counter once per node (node_seed) and gives population p
+// the top 13 bits of seed * K_p, K_p an odd constant per population -- one multiply
+// per store instead of a hash per store.  v is the node's post-collision rest
+// population, a function of every pulled value (through rho and C), so it is
+// non-finite whenever any stored value is: the seed is then 0 and no random bits
+// are added, which keeps a NaN a NaN (added to a NaN pattern such as 0x7fffffff
+// they would carry into the sign bit).  The value's bits do not enter the hash: a
+// seed drawn from them repeats whenever the node's state does, and a node at rest
+// then rounds the same way step after step (a steady mass drift: 36 mass units in
+// 5000 steps of a 64^3 droplet box, against 1.0 for FP32 storage).
+__device__ __forceinline__ uint32_t node_seed(float v, unsigned t, uint32_t step) {
+  uint32_t h = ((t * 0x85EBCA6Bu) ^ (step * 0xC2B2AE35u)) * 0x9E3779B9u;
   h ^= h >> 15;
   h *= 0x2C1B3C6Du;
   h ^= h >> 13;
@@ -152,31 +176,33 @@ __device__ __forceinline__ uint32_t pack_half2_rz(float lo, float hi) {
 
 template <>
 struct Store<__half> {
-  // FP16 deviations from the reference equilibria: f^r_i - w_i, f^p_i, g_j - w_j, in
-  // the slot layout above (the f^r_i / f^p_i pair of a slot in one 32-bit word).
+  // FP16 deviations from the reference equilibria, 2^12 (f^r_i - w~_i), 2^12 f^p_i,
+  // 2^12 (g_j - w_j) with w~ the weights on the 2^-20 grid (WREF), in the slot layout
+  // above (the f^r_i / f^p_i pair of a slot in one 32-bit word).
   static __device__ __forceinline__ unsigned hidx(unsigned ns, unsigned p, unsigned t) { return pop_index(ns, p, t); }
   static __device__ __forceinline__ float ld(const __half *__restrict__ f, unsigned ns, unsigned p, unsigned t) {
-    return __half2float(f[hidx(ns, p, t)]) + pop_ref(p);
+    return fmaf(__half2float(f[hidx(ns, p, t)]), kHalfUnscale, pop_ref(p));
   }
   static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v) {
-    f[hidx(ns, p, t)] = half_stochastic(v - pop_ref(p), p * ns + t);
+    f[hidx(ns, p, t)] = half_stochastic(fmaf(v, kHalfScale, -kHalfScale * pop_ref(p)), p * ns + t);
   }
   // the same rounding with the random word r supplied by the caller (top 13 bits
   // used); the caller passes r = 0 for a node with a non-finite value (node_seed)
   static __device__ __forceinline__ void st_r(__half *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v,
                                               uint32_t r) {
-    f[hidx(ns, p, t)] = __float2half_rz(__uint_as_float(__float_as_uint(v - pop_ref(p)) + (r >> 19)));
+    const float d = fmaf(v, kHalfScale, -kHalfScale * pop_ref(p));
+    f[hidx(ns, p, t)] = __float2half_rz(__uint_as_float(__float_as_uint(d) + (r >> 19)));
   }
   static __device__ __forceinline__ void ld2(const __half *__restrict__ f, unsigned ns, unsigned i, unsigned t,
                                              int iref, float &a, float &b) {
     const float2 v = __half22float2(reinterpret_cast<const __half2 *>(f)[i * ns + t]);
-    a = v.x + W[iref];
-    b = v.y + 0.f;   // the reference of f^p is 0 (the addition maps -0 to +0, as ld does)
+    a = fmaf(v.x, kHalfUnscale, WREF[iref]);
+    b = fmaf(v.y, kHalfUnscale, 0.f);   // the reference of f^p is 0 (as in ld)
   }
   static __device__ __forceinline__ void st2_r(__half *__restrict__ f, unsigned ns, unsigned i, unsigned t, float a,
                                                float b, uint32_t ra, uint32_t rb) {
-    const float ua = __uint_as_float(__float_as_uint(a - W[i]) + (ra >> 19));
-    const float ub = __uint_as_float(__float_as_uint(b) + (rb >> 19));
+    const float ua = __uint_as_float(__float_as_uint(fmaf(a, kHalfScale, -kHalfScale * WREF[i])) + (ra >> 19));
+    const float ub = __uint_as_float(__float_as_uint(b * kHalfScale) + (rb >> 19));
     reinterpret_cast<uint32_t *>(f)[i * ns + t] = pack_half2_rz(ua, ub);
   }
 };
@@ -676,7 +702,7 @@ __global__ void __launch_bounds__(256) k_fields_march(const Inst *__restrict__ i
 // fluid node of plane nz - 1 (same arithmetic as write_outlet_ghost)
 template <typename T>
 __device__ __forceinline__ void write_outlet_ghost_c(int ns_, T *__restrict__ f, unsigned gs, const float (&fr)[Q],
-                                                     const float (&fp)[Q], float g5, float rho_out) {
+                                                     const float (&fp)[Q], float g5, float rho_out, uint32_t seed) {
   float rho = 0.f, rr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -696,10 +722,10 @@ __device__ __forceinline__ void write_outlet_ghost_c(int ns_, T *__restrict__ f,
   for (int i = 0; i < Q; ++i) {
     if (CZ[i] != -1) continue;
     const float corr = feq19(i, rho_out - rho, vx, vy, vz, vv);
-    Store<T>::st(f, ns, i, gs, fr[i] + psi * corr);
-    Store<T>::st(f, ns, Q + i, gs, fp[i] + (1.0f - psi) * corr);
+    Store<T>::st_r(f, ns, i, gs, fr[i] + psi * corr, pop_random(seed, NPOP + i));
+    Store<T>::st_r(f, ns, Q + i, gs, fp[i] + (1.0f - psi) * corr, pop_random(seed, NPOP + Q + i));
   }
-  Store<T>::st(f, ns, 2 * Q + 5, gs, g5);
+  Store<T>::st_r(f, ns, 2 * Q + 5, gs, g5, pop_random(seed, NPOP + 2 * Q + 5));
 }
 
 // a1, a2, a6 - a10 over the fluid slots; stores are coalesced and whole-sector.
@@ -710,11 +736,16 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
                                                                T *__restrict__ fout, const int *__restrict__ gidx,
                                                                const uint32_t *__restrict__ link,
                                                                const float4 *__restrict__ nrm, double *__restrict__ acc,
-                                                               int slot, float *__restrict__ dbg_H,
+                                                               int slot, uint32_t *__restrict__ rstep,
+                                                               float *__restrict__ dbg_H,
                                                                float *__restrict__ dbg_delta) {
   pdl_begin();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  // step counter of the FP16 rounding: read from this step's slot, the next value
+  // written to the other one (read by the next step's main kernel)
+  const uint32_t step = rstep[slot];
   if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) rstep[slot ^ 1] = step + 1u;
     if (BATCH) {
       for (int k = threadIdx.x; k < n_inst; k += blockDim.x) acc[4 * k + 2 + (slot ^ 1)] = 0.0;
     } else if (threadIdx.x == 0) {
@@ -746,7 +777,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     const unsigned ns = (unsigned)S.ns;
     // FP16 rounding bits (unused for FP32); fr + fp of the rest population sums rho
     // and, in reaction mode 0, g[6] carries C: both enter the finiteness check
-    const uint32_t seed = node_seed(fr[Q - 1] + fp[Q - 1] + (I.P.reaction_mode == 0 ? g[Q7 - 1] : 0.f), t);
+    const uint32_t seed = node_seed(fr[Q - 1] + fp[Q - 1] + (I.P.reaction_mode == 0 ? g[Q7 - 1] : 0.f), t, step);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       Store<T>::st2_r(fout, ns, i, t, fr[i], fp[i], pop_random(seed, i), pop_random(seed, Q + i));
@@ -762,7 +793,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     }
     if (I.L.bc_z == 1 && z == I.L.nz - 1) {
       const unsigned gs = (unsigned)(I.ghost + I.L.plane) + (unsigned)(y * I.L.nx + x);
-      write_outlet_ghost_c<T>(S.ns, fout, gs, fr, fp, g5, I.P.rho_out);
+      write_outlet_ghost_c<T>(S.ns, fout, gs, fr, fp, g5, I.P.rho_out, seed);
     }
     if (dbg_H) dbg_H[noff + node] = H;
     if (dbg_delta) dbg_delta[noff + node] = delta;
@@ -851,7 +882,8 @@ __global__ void k_ghost_init_c(Inst I, int ns_, const int *__restrict__ gidx, fl
       Store<T>::ld2(fa, ns, i, (unsigned)s, i, fr[i], fp[i]);
     }
     const float g5 = Store<T>::ld(fa, ns, 2 * Q + 5, (unsigned)s);
-    write_outlet_ghost_c<T>(ns_, fa, gout, fr, fp, g5, rho_out);
+    write_outlet_ghost_c<T>(ns_, fa, gout, fr, fp, g5, rho_out,
+                            node_seed(fr[Q - 1] + fp[Q - 1] + g5, gout, 0xFFFFFFFFu));
   }
 }
 

@@ -394,7 +394,8 @@ __global__ void k_adj_seed(Slots S, const __grid_constant__ Inst I, const float 
 __global__ void __launch_bounds__(128, 3) k_adj_collide(Slots S, const __grid_constant__ Inst I,
                                                      const float *__restrict__ fin, const int *__restrict__ gidx,
                                                      const uint32_t *__restrict__ link,
-                                                     const float4 *__restrict__ nrm, const float *__restrict__ lam,
+                                                     const float4 *__restrict__ nrm, const float *__restrict__ Hs,
+                                                     const float *__restrict__ lam,
                                                      float *__restrict__ fbar, float4 *__restrict__ nbar,
                                                      float *__restrict__ hbar, float *__restrict__ rho_out) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,8 +409,12 @@ __global__ void __launch_bounds__(128, 3) k_adj_collide(Slots S, const __grid_co
   const unsigned node = St.own;
   const uint32_t lk = link[node];
   const float4 nme = nrm[node];
-  const float H =
-      nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nrm[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
+  // the curvature of the forward step: stored by the recompute's main kernel (Hs), or computed here
+  float H;
+  if (Hs)
+    H = Hs[node];
+  else
+    H = nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nrm[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
   PullOffsets O;
   O.init(I.L, x, y, z);
   float fr[Q], fp[Q], g[Q7];

@@ -59,6 +59,7 @@ struct Batch {
   uint32_t *rstep = nullptr;          // step counter of the FP16 rounding bits (two entries, by step parity)
   float *dbg_H = nullptr, *dbg_delta = nullptr;
   bool debug = false;
+  float *h_out = nullptr;             // the main kernel's curvature per node, when set (adjoint recompute)
   size_t device_bytes = 0;
   int64_t step = 0;
   int sticky = LBM_OK;
@@ -83,6 +84,7 @@ struct Batch {
     std::vector<float *> store;   // the states of one segment, recomputed
     std::vector<float *> seg_rhoN;     // rho^N of each state of the segment (dense)
     std::vector<float4 *> seg_nrm;     // wetted normals and |grad rho^N| of each state
+    std::vector<float *> seg_H;        // curvature H of each state (written by the recompute's main kernel)
     float *lam0 = nullptr, *lam1 = nullptr, *fbar = nullptr;   // slot-space adjoints
     float *hbar = nullptr, *rho = nullptr, *rnbar = nullptr;   // dense per-node fields
     float4 *nbar = nullptr;
@@ -165,6 +167,7 @@ void free_all(Batch &b) {
   for (float *p : a.store) cudaFree(p);
   for (float *p : a.seg_rhoN) cudaFree(p);
   for (float4 *p : a.seg_nrm) cudaFree(p);
+  for (float *p : a.seg_H) cudaFree(p);
   void *aptrs[] = {a.lam0, a.lam1, a.fbar, a.hbar, a.rho, a.rnbar, a.nbar, a.coef, a.thbar, a.uin};
   for (void *p : aptrs) cudaFree(p);
   a = Batch::Adj{};
@@ -315,7 +318,7 @@ template <typename T, bool BT>
 void launch_main_t(const Batch &b, cudaStream_t st, const void *fin, void *fout, double *acc, int slot) {
   const Slots S = slots(b);
   const Inst &I = b.h[0].d;
-  float *dh = b.debug ? b.dbg_H : nullptr, *dd = b.debug ? b.dbg_delta : nullptr;
+  float *dh = b.h_out ? b.h_out : (b.debug ? b.dbg_H : nullptr), *dd = b.debug ? b.dbg_delta : nullptr;
   const T *fi = (const T *)fin;
   T *fo = (T *)fout;
   const int *gi = b.gidx;
@@ -1184,11 +1187,13 @@ int adj_alloc(Batch &b, int64_t nseg, int64_t K) {
     float *p = nullptr;
     float *r = nullptr;
     float4 *q = nullptr;
+    float *h = nullptr;
     if (!grab((void **)&p, sb) || !grab((void **)&r, nodes * sizeof(float)) ||
-        !grab((void **)&q, nodes * sizeof(float4))) {
+        !grab((void **)&q, nodes * sizeof(float4)) || !grab((void **)&h, nodes * sizeof(float))) {
       cudaFree(p);
       cudaFree(r);
       cudaFree(q);
+      cudaFree(h);
       return LBM_ENOMEM;
     }
     // interior solids are never written and read as zero by the stencils
@@ -1197,11 +1202,13 @@ int adj_alloc(Batch &b, int64_t nseg, int64_t K) {
       cudaFree(p);
       cudaFree(r);
       cudaFree(q);
+      cudaFree(h);
       return LBM_ECUDA;
     }
     a.store.push_back(p);
     a.seg_rhoN.push_back(r);
     a.seg_nrm.push_back(q);
+    a.seg_H.push_back(h);
   }
   return LBM_OK;
 }
@@ -1257,7 +1264,7 @@ void launch_fields(Batch &b, cudaStream_t st, const float *fin) {
 
 // lambda_t from lambda_{t+1} (lam_in) and the state f_t, whose forward fields are
 // in b.rhoN / b.nrm
-int reverse_step(Batch &b, const float *ft, const float *lam_in, float *lam_out) {
+int reverse_step(Batch &b, const float *ft, const float *Hs, const float *lam_in, float *lam_out) {
   Batch::Adj &a = b.adj;
   const cudaStream_t st = b.stream;
   const Slots S = slots(b);
@@ -1266,7 +1273,7 @@ int reverse_step(Batch &b, const float *ft, const float *lam_in, float *lam_out)
   const unsigned gb = (unsigned)((b.n_bnd + 255) / 256);
   CK(cudaMemsetAsync(a.nbar, 0, (size_t)b.nodes * sizeof(float4), st));
   CK(cudaMemsetAsync(a.rnbar, 0, (size_t)b.nodes * sizeof(float), st));
-  k_adj_collide<<<g128, 128, 0, st>>>(S, I, ft, b.gidx, b.link, b.nrm, lam_in, a.fbar, a.nbar, a.hbar, a.rho);
+  k_adj_collide<<<g128, 128, 0, st>>>(S, I, ft, b.gidx, b.link, b.nrm, Hs, lam_in, a.fbar, a.nbar, a.hbar, a.rho);
   k_adj_curv<<<g256, 256, 0, st>>>(S, I, b.nrm, a.hbar, a.nbar);
   if (b.n_bnd > 0) k_adj_nsolid<<<gb, 256, 0, st>>>(I, b.bnd, b.n_bnd, b.link, b.nrm, a.nbar);
   k_adj_normal<<<g256, 256, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, a.nbar, a.rnbar, a.thbar);
@@ -1302,19 +1309,23 @@ int adjoint_backward(Batch &b, double seed, double *dtheta, double *du_in, float
   for (int64_t s = a.nseg - 1; s >= 0 && rc == LBM_OK; --s) {
     const int64_t t0 = s * a.K, t1 = std::min(t0 + a.K, a.nsteps);
     CK(cudaMemcpyAsync(a.store[0], a.cp[s], sb, cudaMemcpyDeviceToDevice, b.stream));
-    // recompute the segment, keeping every state and its forward fields
+    // recompute the segment, keeping every state, its forward fields and (from the
+    // main kernel) its curvature; the last state of the segment has no main step,
+    // and the collide kernel computes its curvature itself
     for (int64_t t = t0; t < t1; ++t) {
       const int64_t j = t - t0;
       b.rhoN = a.seg_rhoN[j];
       b.nrm = a.seg_nrm[j];
       launch_fields(b, b.stream, a.store[j]);
+      b.h_out = a.seg_H[j];
       if (t + 1 < t1) launch_main<float>(b, b.stream, a.store[j], a.store[j + 1], b.acc_scratch, 0);
+      b.h_out = nullptr;
     }
     if (cudaGetLastError() != cudaSuccess) rc = LBM_ECUDA;
     for (int64_t t = t1 - 1; t >= t0 && rc == LBM_OK; --t) {
       b.rhoN = a.seg_rhoN[t - t0];
       b.nrm = a.seg_nrm[t - t0];
-      rc = reverse_step(b, a.store[t - t0], lam, lamn);
+      rc = reverse_step(b, a.store[t - t0], t + 1 < t1 ? a.seg_H[t - t0] : nullptr, lam, lamn);
       std::swap(lam, lamn);
     }
   }

@@ -9,16 +9,26 @@
 // recomputed from f_t by the forward kernels before the reverse kernels run:
 //
 //   collide   per fluid node: local adjoint of a2, a7 - a10 and of the outlet
-//             ghost (non-equilibrium extrapolation) -> F_bar (pulled
-//             populations), n_bar, |grad|_bar, H_bar, rho
+//             ghost (non-equilibrium extrapolation), then the transpose of a1
+//             (streaming, bounce-back, ghosts) as a push: the adjoint of each
+//             pulled population goes to the stored population it came from
+//             -> lambda_t without its density term (below), n_bar,
+//             |grad|_bar, H_bar, rho, and the inlet ghost's share of dJ/du_in
 //   curv      per interface node: transpose of the curvature stencil a6 -> n_bar
 //   nsolid    per boundary solid: transpose of the solid-normal average -> n_bar
 //   normal    per fluid node: transpose of a5 (wetting) and a4 (normalisation,
 //             gradient stencil) -> rho^N_bar, theta_bar
 //   csolid    per boundary solid: transpose of the solid-colour average a3
-//   coef      per fluid node: d rho^N / d f coefficients times rho^N_bar
-//   pull      per slot: transpose of a1 (streaming, bounce-back, ghosts)
-//             -> lambda_t, dJ/du_in from the inlet ghost plane
+//   coef      per fluid node: d rho^N / d f coefficients times rho^N_bar, and
+//             their share of dJ/du_in on plane 0
+//
+// A stored population of f_t enters the step through the node y that pulls it:
+// through y's collision (the push above) and through rho^N(y) (a4).  The second
+// term, coef(y), is known only after the stencil transposes, so lambda is kept
+// without it and the collide kernel of the next reverse step adds coef(y) as it
+// reads lambda_{t+1}; k_adj_finish adds it to lambda_0.  Each stored population
+// is pulled by exactly one node or by none (it leaves the column): the push needs
+// no atomics, and the owner of a population that leaves writes its zero.
 //
 // Branch decisions (the 1e-5 / 1e-6 thresholds, the n_+ / n_- choice, the
 // reaction clamps) are those of the forward values, i.e. frozen.  Stencil
@@ -390,73 +400,150 @@ __global__ void k_adj_seed(Slots S, const __grid_constant__ Inst I, const float 
   for (int j = 0; j < Q7; ++j) lam[(unsigned)(2 * Q + j) * ns + t] = a * jz * inv;
 }
 
-// collide: local adjoint at every fluid slot
+// collide: local adjoint at every fluid slot and the push of a1's transpose
+// lam_in: lambda_{t+1} without its density terms, coef_in the coefficients of the
+// reverse step t + 1 (zero for the objective's seed); lam_out: lambda_t without
+// its density terms.
 __global__ void __launch_bounds__(128, 3) k_adj_collide(Slots S, const __grid_constant__ Inst I,
                                                      const float *__restrict__ fin, const int *__restrict__ gidx,
                                                      const uint32_t *__restrict__ link,
                                                      const float4 *__restrict__ nrm, const float *__restrict__ Hs,
-                                                     const float *__restrict__ lam,
-                                                     float *__restrict__ fbar, float4 *__restrict__ nbar,
-                                                     float *__restrict__ hbar, float *__restrict__ rho_out) {
+                                                     const float *__restrict__ lam, const float2 *__restrict__ coef_in,
+                                                     float u_in, float c_in, float *__restrict__ lam_out,
+                                                     float4 *__restrict__ nbar, float *__restrict__ hbar,
+                                                     float *__restrict__ rho_out, double *__restrict__ uin_acc) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)S.nslots) return;
-  const uint32_t pk = S.node[t];
-  if (pk == kNoNode) return;
-  int x, y, z;
-  unpack(pk, x, y, z);
-  StencilOffsets St;
-  St.init(I.L, x, y, z);
-  const unsigned node = St.own;
-  const uint32_t lk = link[node];
-  const float4 nme = nrm[node];
-  // the curvature of the forward step: stored by the recompute's main kernel (Hs), or computed here
-  float H;
-  if (Hs)
-    H = Hs[node];
-  else
-    H = nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nrm[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
-  PullOffsets O;
-  O.init(I.L, x, y, z);
-  float fr[Q], fp[Q], g[Q7];
-  pull_compact<float>(S.ns, I.P, fin, gidx, O, t, fr, fp, g);
-  const unsigned ns = (unsigned)S.ns;
-  float lr[Q], lp[Q], lg[Q7];
+  double du = 0.0;
+  const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
+  if (pk != kNoNode) {
+    int x, y, z;
+    unpack(pk, x, y, z);
+    const Lattice &L = I.L;
+    StencilOffsets St;
+    St.init(L, x, y, z);
+    const unsigned node = St.own;
+    const uint32_t lk = link[node];
+    const float4 nme = nrm[node];
+    // the curvature of the forward step: stored by the recompute's main kernel (Hs), or computed here
+    float H;
+    if (Hs)
+      H = Hs[node];
+    else
+      H = nme.w >= GRAD_EPS ? curvature(nme, [&](int i) { return nrm[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
+    PullOffsets O;
+    O.init(L, x, y, z);
+    int src[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    lr[i] = lam[(unsigned)i * ns + t];
-    lp[i] = lam[(unsigned)(Q + i) * ns + t];
-  }
-#pragma unroll
-  for (int j = 0; j < Q7; ++j) lg[j] = lam[(unsigned)(2 * Q + j) * ns + t];
-  if (I.L.bc_z == 1 && z == I.L.nz - 1) {
-    // the outlet ghost above this node is a function of its post-collision populations
-    const unsigned gs = (unsigned)(I.ghost + I.L.plane) + (unsigned)(y * I.L.nx + x);
-    float sr[Q], sp[Q], sg[Q7], gr[Q], gp[Q];
+    for (int i = 0; i < Q - 1; ++i) src[i] = __ldg(gidx + O.src(CX[i], CY[i], CZ[i]));
+    src[Q - 1] = (int)t;
+    const unsigned ns = (unsigned)S.ns;
+    float fr[Q], fp[Q], g[Q7];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      sr[i] = fr[i];
-      sp[i] = fp[i];
-      gr[i] = CZ[i] == -1 ? lam[(unsigned)i * ns + gs] : 0.f;
-      gp[i] = CZ[i] == -1 ? lam[(unsigned)(Q + i) * ns + gs] : 0.f;
+      const bool bb = src[i] < 0;
+      Store<float>::ld2(fin, ns, bb ? (unsigned)OPP[i] : (unsigned)i, bb ? t : (unsigned)src[i], i, fr[i], fp[i]);
     }
 #pragma unroll
-    for (int j = 0; j < Q7; ++j) sg[j] = g[j];
-    collide_node(I.P, lk, sr, sp, sg, nme, H);
-    outlet_ghost_adj(sr, sp, I.P.rho_out, gr, gp, lr, lp);
-    lg[5] += lam[(unsigned)(2 * Q + 5) * ns + gs];
-  }
-  float nbx, nby, nbz, wb, Hb;
-  const float rho = collide_node_adj(I.P, lk, fr, fp, g, nme, H, lr, lp, lg, nbx, nby, nbz, wb, Hb);
+    for (int j = 0; j < Q7; ++j) {
+      const int d = GDIR[j];
+      const bool bb = src[d] < 0;
+      g[j] = Store<float>::ld(fin, ns, 2 * Q + (bb ? GOPP[j] : j), bb ? t : (unsigned)src[d]);
+    }
+    // lambda_{t+1} of this slot's populations, each with the density term of the node
+    // that pulls it: x + c_i when fluid, x itself when x + c_i is solid (bounce-back),
+    // none when x + c_i leaves the column
+    float lr[Q], lp[Q], lg[Q7];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    fbar[(unsigned)i * ns + t] = lr[i];
-    fbar[(unsigned)(Q + i) * ns + t] = lp[i];
-  }
+    for (int i = 0; i < Q; ++i) {
+      lr[i] = lam[(unsigned)i * ns + t];
+      lp[i] = lam[(unsigned)(Q + i) * ns + t];
+      const int zt = z + CZ[i];
+      if (L.bc_z == 0 || (zt >= 0 && zt < L.nz)) {
+        const bool solid = i < Q - 1 && ((lk >> OPP[i]) & 1u);   // x + c_i is the source of direction OPP[i]
+        const float2 c2 = __ldg(coef_in + ((i == Q - 1 || solid) ? node : St.nb(CX[i], CY[i], CZ[i])));
+        lr[i] += c2.x;
+        lp[i] += c2.y;
+      }
+    }
 #pragma unroll
-  for (int j = 0; j < Q7; ++j) fbar[(unsigned)(2 * Q + j) * ns + t] = lg[j];
-  nbar[node] = make_float4(nbx, nby, nbz, wb);
-  hbar[node] = nme.w >= GRAD_EPS ? Hb : 0.f;
-  rho_out[node] = rho;
+    for (int j = 0; j < Q7; ++j) lg[j] = lam[(unsigned)(2 * Q + j) * ns + t];
+    if (L.bc_z == 1 && z == L.nz - 1) {
+      // the outlet ghost above this node is a function of its post-collision populations;
+      // its population i (c_z = -1) is pulled by the fluid node x + (c_x, c_y, 0) of this plane
+      const unsigned gs = (unsigned)(I.ghost + L.plane) + (unsigned)(y * L.nx + x);
+      float sr[Q], sp[Q], sg[Q7], gr[Q], gp[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        sr[i] = fr[i];
+        sp[i] = fp[i];
+        gr[i] = 0.f;
+        gp[i] = 0.f;
+        if (CZ[i] == -1) {
+          gr[i] = lam[(unsigned)i * ns + gs];
+          gp[i] = lam[(unsigned)(Q + i) * ns + gs];
+          const int xd = x + CX[i] < 0 ? L.nx - 1 : (x + CX[i] >= L.nx ? 0 : x + CX[i]);
+          const int yd = y + CY[i] < 0 ? L.ny - 1 : (y + CY[i] >= L.ny ? 0 : y + CY[i]);
+          const long long dn = ((long long)z * L.ny + yd) * L.nx + xd;
+          if (!(link[dn] & BIT_SOLID)) {
+            const float2 c2 = __ldg(coef_in + dn);
+            gr[i] += c2.x;
+            gp[i] += c2.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < Q7; ++j) sg[j] = g[j];
+      collide_node(I.P, lk, sr, sp, sg, nme, H);
+      outlet_ghost_adj(sr, sp, I.P.rho_out, gr, gp, lr, lp);
+      lg[5] += lam[(unsigned)(2 * Q + 5) * ns + gs];
+    }
+    float nbx, nby, nbz, wb, Hb;
+    const float rho = collide_node_adj(I.P, lk, fr, fp, g, nme, H, lr, lp, lg, nbx, nby, nbz, wb, Hb);
+    // push: the adjoint of each pulled population to the population it was pulled from
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const bool bb = src[i] < 0;
+      const unsigned s_ = bb ? t : (unsigned)src[i], pr = bb ? (unsigned)OPP[i] : (unsigned)i;
+      lam_out[pr * ns + s_] = lr[i];
+      lam_out[(Q + pr) * ns + s_] = lp[i];
+    }
+#pragma unroll
+    for (int j = 0; j < Q7; ++j) {
+      const int d = GDIR[j];
+      const bool bb = src[d] < 0;
+      lam_out[(unsigned)(2 * Q + (bb ? GOPP[j] : j)) * ns + (bb ? t : (unsigned)src[d])] = lg[j];
+    }
+    if (L.bc_z == 1) {
+      // populations of this slot that leave the column: pulled by nobody, adjoint 0
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if ((z == 0 && CZ[i] == -1) || (z == L.nz - 1 && CZ[i] == 1)) {
+          lam_out[(unsigned)i * ns + t] = 0.f;
+          lam_out[(unsigned)(Q + i) * ns + t] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < Q7; ++j) {
+        const int cz = CZ[GDIR[j]];
+        if ((z == 0 && cz == -1) || (z == L.nz - 1 && cz == 1)) lam_out[(unsigned)(2 * Q + j) * ns + t] = 0.f;
+      }
+      // the inlet ghost's populations entering at plane 0: f^r_i = f^eq_i(1, u_in z)
+      // (c_iz = 1), g_4 = w_4 c_in (1 + 4 u_in); here without their density terms (k_adj_coef)
+      if (z == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          if (CZ[i] == 1) s += (double)lr[i] * (double)(W[i] * (3.0f + 6.0f * u_in));
+        s += (double)lg[4] * (double)(4.0f * W7[4] * c_in);
+        du = s;
+      }
+    }
+    nbar[node] = make_float4(nbx, nby, nbz, wb);
+    hbar[node] = nme.w >= GRAD_EPS ? Hb : 0.f;
+    rho_out[node] = rho;
+  }
+  du = warp_sum(du);
+  if ((threadIdx.x & 31) == 0 && du != 0.0) atomicAdd(uin_acc, du);
 }
 
 // curv: H = -sum_i 3 w_i (c_i - (n.c_i) n) . n(x + c_i); dH/dn = (D + D^T) n
@@ -637,107 +724,68 @@ __global__ void k_adj_csolid(const __grid_constant__ Inst I, const uint32_t *__r
 }
 
 // coef: rho^N = (rho^r - rho^p) / rho  ->  d/d f^r_i = (1 - rho^N)/rho, d/d f^p_i = -(1 + rho^N)/rho
+// On plane 0 of a column the pulled f^r_i with c_iz = 1 are the inlet ghost's, so their
+// density terms add to dJ/du_in.
 __global__ void k_adj_coef(Slots S, const __grid_constant__ Inst I, const float *__restrict__ rhoN,
-                           const float *__restrict__ rho, const float *__restrict__ rnbar,
-                           float2 *__restrict__ coef) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)S.nslots) return;
-  const uint32_t pk = S.node[t];
-  if (pk == kNoNode) return;
-  int x, y, z;
-  unpack(pk, x, y, z);
-  const long long node = nidx(I.L, x, y, z);
-  const float rb = rnbar[node], r = rhoN[node], inv = 1.0f / rho[node];
-  coef[node] = make_float2(rb * (1.0f - r) * inv, -rb * (1.0f + r) * inv);
-}
-
-// pull: transpose of a1.  Population p of slot y leaves along c_p: pulled by the
-// fluid node y + c_p, bounced back into y when y + c_p is solid, or dropped when
-// y + c_p lies outside the column.  Inlet ghost slots give dJ/du_in.
-__global__ void __launch_bounds__(256) k_adj_pull(Slots S, const __grid_constant__ Inst I,
-                                                  const int *__restrict__ gidx, const float *__restrict__ fbar,
-                                                  const float2 *__restrict__ coef, float u_in, float c_in,
-                                                  float *__restrict__ lam, double *__restrict__ uin_acc) {
+                           const float *__restrict__ rho, const float *__restrict__ rnbar, float u_in,
+                           float2 *__restrict__ coef, double *__restrict__ uin_acc) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   double du = 0.0;
-  if (t < (unsigned)S.nslots) {
-    const Lattice &L = I.L;
-    const unsigned ns = (unsigned)S.ns;
-    const uint32_t pk = S.node[t];
-    if (pk != kNoNode) {
-      // fluid slot: the 19 destinations once (slot, or -1 solid, or -2 outside the column)
-      int x, y, z;
-      unpack(pk, x, y, z);
-      PullOffsets O;
-      O.init(L, x, y, z);
-      StencilOffsets St;
-      St.init(L, x, y, z);
-      // branch-free: every load is issued (the bounce-back and dropped cases read
-      // the node's own slot and are selected or zeroed afterwards)
-      int tgt[Q];
-      float2 cf[Q];
+  const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
+  if (pk != kNoNode) {
+    int x, y, z;
+    unpack(pk, x, y, z);
+    const long long node = nidx(I.L, x, y, z);
+    const float rb = rnbar[node], r = rhoN[node], inv = 1.0f / rho[node];
+    const float2 c2 = make_float2(rb * (1.0f - r) * inv, -rb * (1.0f + r) * inv);
+    coef[node] = c2;
+    if (I.L.bc_z == 1 && z == 0) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int zt = z + CZ[i];
-        const bool inside = L.bc_z == 0 || (zt >= 0 && zt < L.nz);
-        const unsigned gi = inside ? O.src(-CX[i], -CY[i], -CZ[i]) : O.own;
-        const int s_ = __ldg(gidx + gi);
-        tgt[i] = inside ? s_ : -2;
-        cf[i] = __ldg(coef + (tgt[i] >= 0 ? St.nb(CX[i], CY[i], CZ[i]) : St.own));
-      }
-#pragma unroll
-      for (int p = 0; p < NPOP; ++p) {
-        int d, po;
-        if (p < 2 * Q) {
-          d = p % Q;
-          po = p - d + OPP[d];
-        } else {
-          d = GDIR[p - 2 * Q];
-          po = 2 * Q + GOPP[p - 2 * Q];
-        }
-        const bool pulled = tgt[d] >= 0;
-        const int pp = pulled ? p : po;
-        const unsigned addr = (unsigned)pp * ns + (pulled ? (unsigned)tgt[d] : t);
-        float v = __ldg(fbar + addr);
-        // coefficient of the destination node (its own coefficient for bounce-back)
-        if (pp < Q) v += cf[d].x;
-        else if (pp < 2 * Q) v += cf[d].y;
-        lam[(unsigned)p * ns + t] = tgt[d] == -2 ? 0.f : v;
-      }
-    } else {
-      // ghost slot (column mode): only the populations entering the column are used
-      const long long q = (long long)t - I.ghost;
-      const bool inlet = q < L.plane;
-      const int z = inlet ? -1 : L.nz;
-      const long long r = inlet ? q : q - L.plane;
-      const int y = (int)(r / L.nx), x = (int)(r % L.nx);
-      double s = 0.0;
-      for (int p = 0; p < NPOP; ++p) {
-        const int d = p < 2 * Q ? p % Q : GDIR[p - 2 * Q];
-        float v = 0.f;
-        if (CZ[d] == (inlet ? 1 : -1)) {
-          const int xt = (x + CX[d] + L.nx) % L.nx, yt = (y + CY[d] + L.ny) % L.ny, zt = z + CZ[d];
-          const int st = gidx[(long long)(zt + 1) * L.plane + (long long)yt * L.nx + xt];
-          if (st >= 0) {
-            v = fbar[(unsigned)p * ns + (unsigned)st];
-            if (p < 2 * Q) {
-              const float2 c2 = coef[nidx(L, xt, yt, zt)];
-              v += p < Q ? c2.x : c2.y;
-            }
-          }
-        }
-        lam[(unsigned)p * ns + t] = v;
-        // inlet ghost: f^r_i = f^eq_i(1, u_in z) for c_iz = 1, g_4 = w_4 c_in (1 + 4 u_in)
-        if (inlet && v != 0.f) {
-          if (p < Q) s += (double)v * (double)(W[p] * (3.0f + 6.0f * u_in));
-          if (p == 2 * Q + 4) s += (double)v * (double)(4.0f * W7[4] * c_in);
-        }
-      }
-      du = s;
+      for (int i = 0; i < Q; ++i)
+        if (CZ[i] == 1) du += (double)c2.x * (double)(W[i] * (3.0f + 6.0f * u_in));
     }
   }
   du = warp_sum(du);
   if ((threadIdx.x & 31) == 0 && du != 0.0) atomicAdd(uin_acc, du);
+}
+
+// lambda_0 with its density terms: every population of a fluid slot, and the outlet
+// ghost's populations entering the column (read by k_adj_ghost0), gain coef of the
+// node that pulls them (the same rule as the collide kernel's read of lambda_{t+1})
+__global__ void k_adj_finish(Slots S, const __grid_constant__ Inst I, const uint32_t *__restrict__ link,
+                             const float2 *__restrict__ coef, float *__restrict__ lam) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)S.nslots) return;
+  const Lattice &L = I.L;
+  const unsigned ns = (unsigned)S.ns;
+  const uint32_t pk = S.node[t];
+  if (pk != kNoNode) {
+    int x, y, z;
+    unpack(pk, x, y, z);
+    StencilOffsets St;
+    St.init(L, x, y, z);
+    const uint32_t lk = link[St.own];
+    for (int i = 0; i < Q; ++i) {
+      const int zt = z + CZ[i];
+      if (L.bc_z == 1 && (zt < 0 || zt >= L.nz)) continue;
+      const bool solid = i < Q - 1 && ((lk >> OPP[i]) & 1u);
+      const float2 c2 = coef[(i == Q - 1 || solid) ? St.own : St.nb(CX[i], CY[i], CZ[i])];
+      lam[(unsigned)i * ns + t] += c2.x;
+      lam[(unsigned)(Q + i) * ns + t] += c2.y;
+    }
+    return;
+  }
+  if (L.bc_z != 1 || (long long)t < (long long)I.ghost + L.plane) return;   // inlet ghosts: not needed
+  const long long r = (long long)t - I.ghost - L.plane;                       // outlet ghost (x, y, nz)
+  const int y = (int)(r / L.nx), x = (int)(r % L.nx);
+  for (int i = 0; i < Q; ++i) {
+    if (CZ[i] != -1) continue;
+    const int xd = (x + CX[i] + L.nx) % L.nx, yd = (y + CY[i] + L.ny) % L.ny;
+    const long long dn = ((long long)(L.nz - 1) * L.ny + yd) * L.nx + xd;
+    if (link[dn] & BIT_SOLID) continue;
+    lam[(unsigned)i * ns + t] += coef[dn].x;
+    lam[(unsigned)(Q + i) * ns + t] += coef[dn].y;
+  }
 }
 
 // The outlet ghost of the start state is the extrapolation of its plane nz - 1:

@@ -85,7 +85,7 @@ struct Batch {
     std::vector<float *> seg_rhoN;     // rho^N of each state of the segment (dense)
     std::vector<float4 *> seg_nrm;     // wetted normals and |grad rho^N| of each state
     std::vector<float *> seg_H;        // curvature H of each state (written by the recompute's main kernel)
-    float *lam0 = nullptr, *lam1 = nullptr, *fbar = nullptr;   // slot-space adjoints
+    float *lam0 = nullptr, *lam1 = nullptr;   // slot-space adjoints (without their density terms)
     float *hbar = nullptr, *rho = nullptr, *rnbar = nullptr;   // dense per-node fields
     float4 *nbar = nullptr;
     float2 *coef = nullptr;
@@ -168,7 +168,7 @@ void free_all(Batch &b) {
   for (float *p : a.seg_rhoN) cudaFree(p);
   for (float4 *p : a.seg_nrm) cudaFree(p);
   for (float *p : a.seg_H) cudaFree(p);
-  void *aptrs[] = {a.lam0, a.lam1, a.fbar, a.hbar, a.rho, a.rnbar, a.nbar, a.coef, a.thbar, a.uin};
+  void *aptrs[] = {a.lam0, a.lam1, a.hbar, a.rho, a.rnbar, a.nbar, a.coef, a.thbar, a.uin};
   for (void *p : aptrs) cudaFree(p);
   a = Batch::Adj{};
 }
@@ -1171,7 +1171,7 @@ int adj_alloc(Batch &b, int64_t nseg, int64_t K) {
     return true;
   };
   if (!a.lam0) {
-    bool ok = grab((void **)&a.lam0, sb) && grab((void **)&a.lam1, sb) && grab((void **)&a.fbar, sb) &&
+    bool ok = grab((void **)&a.lam0, sb) && grab((void **)&a.lam1, sb) &&
               grab((void **)&a.hbar, nodes * sizeof(float)) && grab((void **)&a.rho, nodes * sizeof(float)) &&
               grab((void **)&a.rnbar, nodes * sizeof(float)) && grab((void **)&a.nbar, nodes * sizeof(float4)) &&
               grab((void **)&a.coef, nodes * sizeof(float2)) && grab((void **)&a.thbar, nodes * sizeof(double)) &&
@@ -1271,16 +1271,17 @@ int reverse_step(Batch &b, const float *ft, const float *Hs, const float *lam_in
   const Inst &I = b.h[0].d;
   const unsigned g128 = (unsigned)((S.nslots + 127) / 128), g256 = (unsigned)((S.nslots + 255) / 256);
   const unsigned gb = (unsigned)((b.n_bnd + 255) / 256);
+  const lbm_params &p = b.h[0].prm;
   CK(cudaMemsetAsync(a.nbar, 0, (size_t)b.nodes * sizeof(float4), st));
   CK(cudaMemsetAsync(a.rnbar, 0, (size_t)b.nodes * sizeof(float), st));
-  k_adj_collide<<<g128, 128, 0, st>>>(S, I, ft, b.gidx, b.link, b.nrm, Hs, lam_in, a.fbar, a.nbar, a.hbar, a.rho);
+  // a.coef holds the coefficients of the reverse step t + 1 until k_adj_coef replaces them
+  k_adj_collide<<<g128, 128, 0, st>>>(S, I, ft, b.gidx, b.link, b.nrm, Hs, lam_in, a.coef, (float)p.u_in,
+                                      (float)p.c_in, lam_out, a.nbar, a.hbar, a.rho, a.uin);
   k_adj_curv<<<g256, 256, 0, st>>>(S, I, b.nrm, a.hbar, a.nbar);
   if (b.n_bnd > 0) k_adj_nsolid<<<gb, 256, 0, st>>>(I, b.bnd, b.n_bnd, b.link, b.nrm, a.nbar);
   k_adj_normal<<<g256, 256, 0, st>>>(S, I, b.rhoN, b.link, b.nsv, a.nbar, a.rnbar, a.thbar);
   if (b.n_bnd > 0) k_adj_csolid<<<gb, 256, 0, st>>>(I, b.bnd, b.n_bnd, b.link, a.rnbar);
-  k_adj_coef<<<g256, 256, 0, st>>>(S, I, b.rhoN, a.rho, a.rnbar, a.coef);
-  const lbm_params &p = b.h[0].prm;
-  k_adj_pull<<<g256, 256, 0, st>>>(S, I, b.gidx, a.fbar, a.coef, (float)p.u_in, (float)p.c_in, lam_out, a.uin);
+  k_adj_coef<<<g256, 256, 0, st>>>(S, I, b.rhoN, a.rho, a.rnbar, (float)p.u_in, a.coef, a.uin);
   CK(cudaGetLastError());
   return LBM_OK;
 }
@@ -1297,6 +1298,10 @@ int adjoint_backward(Batch &b, double seed, double *dtheta, double *du_in, float
   for (int64_t j = 0; j < a.K; ++j) CK(cudaMemcpyAsync(a.store[j], b.fa, sb, cudaMemcpyDeviceToDevice, b.stream));
   CK(cudaMemsetAsync(a.thbar, 0, (size_t)b.nodes * sizeof(double), b.stream));
   CK(cudaMemsetAsync(a.uin, 0, sizeof(double), b.stream));
+  // the objective's seed has no density terms; the ghost populations that no node pulls
+  // are never written by the push and must read 0
+  CK(cudaMemsetAsync(a.coef, 0, (size_t)b.nodes * sizeof(float2), b.stream));
+  CK(cudaMemsetAsync(a.lam1, 0, sb, b.stream));
   const double a_in = seed * a.phi_out / (a.phi_in * a.phi_in), a_out = -seed / a.phi_in;
   const Slots S = slots(b);
   k_adj_seed<<<(unsigned)((S.nslots + 255) / 256), 256, 0, b.stream>>>(S, ih.d, (const float *)b.fa, (float)a_in,
@@ -1340,6 +1345,7 @@ int adjoint_backward(Batch &b, double seed, double *dtheta, double *du_in, float
   CK(cudaStreamSynchronize(b.stream));
   if (du_in) *du_in = u;
   if (dstate) {
+    k_adj_finish<<<(unsigned)((S.nslots + 255) / 256), 256, 0, b.stream>>>(S, ih.d, b.link, a.coef, lam);
     k_adj_ghost0<<<(unsigned)((S.nslots + 255) / 256), 256, 0, b.stream>>>(S, ih.d, a.cp[0], lam);
     CK(cudaGetLastError());
     const int rc = slots_to_host<float, true>(b, 0, lam, dstate, state_bytes);   // adjoint order

@@ -1227,9 +1227,9 @@ int adjoint_forward(Batch &b, int64_t nsteps, int64_t every, double *objective) 
   int rc = adj_alloc(b, nseg, K);
   if (rc) return rc;
   const size_t sb = (size_t)NPOP * b.ns * sizeof(float);
-  for (int64_t s = 0; s < nsteps; ++s) {
-    if (s % K == 0) CK(cudaMemcpyAsync(a.cp[s / K], b.fa, sb, cudaMemcpyDeviceToDevice, b.stream));
-    rc = step_n(b, 1);
+  for (int64_t s = 0; s < nsteps; s += K) {
+    CK(cudaMemcpyAsync(a.cp[s / K], b.fa, sb, cudaMemcpyDeviceToDevice, b.stream));
+    rc = step_n(b, std::min(K, nsteps - s));   // the segment's steps as one run of graph replays
     if (rc) return rc;
   }
   rc = launch_observables(b);

@@ -196,6 +196,13 @@ def bytes_per_fluid_node(params):
     return 2 * width * npop + 1
 
 
+def density_pass_bytes_per_fluid_node(params):
+    """Bytes of the separate density pass (an implementation overhead, not part of the
+    node update): the f^r and f^p of the 19 pulled directions read again, rho^N written."""
+    width = 2 if params.storage == 1 else 4
+    return 2 * 19 * width + 4
+
+
 # --------------------------------------------------------------------------- CPU oracle legs
 def _oracle_params(wl):
     from oracle import cglbm as O
@@ -469,7 +476,15 @@ def run_native(args):
                                     f"x {Nf} fluid nodes",
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.4 TB/s",
-                     "step_effective_gbs": round(alg_bytes / (t_ms / args.steps * 1e-3) / 1e9, 1)},
+                     "step_effective_gbs": round(alg_bytes / (t_ms / args.steps * 1e-3) / 1e9, 1),
+                     "step_frac": round(alg_bytes / (t_ms / args.steps * 1e-3) / 1e9 / peak, 4),
+                     "density_pass_bytes_per_fluid_node": density_pass_bytes_per_fluid_node(head),
+                     "step_effective_gbs_incl_density_pass": round(
+                         Nf * (per_node + density_pass_bytes_per_fluid_node(head)) / (t_ms / args.steps * 1e-3) / 1e9,
+                         1),
+                     "step_frac_incl_density_pass": round(
+                         Nf * (per_node + density_pass_bytes_per_fluid_node(head)) / (t_ms / args.steps * 1e-3) / 1e9
+                         / peak, 4)},
         "kernels": {"source": f"CUDA events around every launch of a separate {psteps}-step run (no graphs)",
                     **kern},
         "variants": variants,

@@ -92,7 +92,9 @@ typedef struct {
   int32_t reaction_mode; /* 0: delta = min(k NN r C psi, C, rho^r), C on D3Q7;
                             1: delta = min(xi NN r, 1) rho^r, C not evolved                  */
   int32_t storage;    /* population storage: 0 = FP32; 1 = FP16 deviations from the resting
-                         reactant equilibrium (f^r - w, f^p, g - w), FP32 arithmetic          */
+                         reactant equilibrium (f^r - w, f^p, g - w, scaled by 2^12, so
+                         deviations up to 16 in magnitude are representable), unbiased
+                         stochastic rounding, FP32 arithmetic                                 */
   void *cuda_stream;  /* cudaStream_t to launch on (borrowed); NULL = legacy default stream  */
 } lbm_params;
 

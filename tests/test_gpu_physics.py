@@ -14,6 +14,13 @@ is resolved:
   started 20 - 40 degrees away from the imposed angle, relax to it within 3 degrees
   at 30, 60, 90, 120 and 150 degrees (30: 31.3 from above and 30.3 from below; 150:
   152.6 from above and below at radius 30, 151.6 at radius 45).
+* Poiseuille flow between halfway bounce-back plates under a body force (the central-
+  moment collision, the force shift and bounce-back): the parabola's curvature is
+  -a / (2 nu) and its centre line a H^2 / (8 nu).
+* Gaussian spreading of the reactant (the D3Q7 transport): the variance grows as 2 D t
+  along each axis.
+* First-order reaction at the wall layers of a channel at rest (a10 with D3Q7 transport):
+  the reactant decays at the rate of the slowest mode of diffusion with that sink.
 """
 import math
 
@@ -126,3 +133,111 @@ def test_contact_angle_large_caps(theta, start, nx, nz, area, steps):
         measured = _measured_angle(L.field(lbm.FIELD_RHON), solid)
     print(f"theta {theta}: {measured:.2f} degrees after {steps} steps from {start}")
     assert abs(measured - theta) < 3.0, measured
+
+
+# --------------------------------------------------------------------- Poiseuille
+def _velocity_x(f, accel_x):
+    fm = f[0:19].astype(np.float64) + f[19:38]
+    rho = fm.sum(axis=0)
+    cx = np.array([1, -1, 0, 0, 0, 0, 1, 1, 1, 1, -1, -1, -1, -1, 0, 0, 0, 0, 0], dtype=np.float64)
+    return np.tensordot(cx, fm, axes=(0, 0)) / np.where(rho > 0, rho, 1.0) + 0.5 * accel_x
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_poiseuille_between_plates(tau):
+    """Plates at z = 0 and z = H + 1 (halfway bounce-back walls), x and y periodic, body
+    force a along x, one phase: after 30 diffusion times the physical velocity u + a/2
+    is the parabola of curvature -a / (2 nu) (least-squares fit over the channel, 1e-3;
+    single second differences carry the FP32 rounding of u, about 1e-2 of their size)
+    with the centre line a H^2 / (8 nu) of halfway walls (1 %)."""
+    H, a = 32, 1e-5
+    shape = (H + 2, 4, 4)
+    solid = np.zeros(shape, bool)
+    solid[0] = solid[-1] = True
+    nu = (tau - 0.5) / 3.0
+    steps = int(30 * H * H / (nu * math.pi ** 2))
+    with lbm.Lattice(solid, lbm.Params(tau=tau, sigma=0.0, k_rate=0.0, accel=(a, 0.0, 0.0)), bc_z=0) as L:
+        L.step(steps)
+        ux = _velocity_x(L.get_state(), a)[1:-1].mean(axis=(1, 2))
+    zc = np.arange(H) - (H - 1) / 2.0
+    c2 = np.polyfit(zc, ux, 2)[0]
+    assert abs(c2 / (-a / (2 * nu)) - 1) < 1e-3, c2 / (-a / (2 * nu))
+    centre = 0.5 * (ux[H // 2 - 1] + ux[H // 2])
+    ref = a * H * H / (8 * nu) * (1 - (0.5 / (H / 2)) ** 2)
+    assert abs(centre / ref - 1) < 0.01, centre / ref
+
+
+# --------------------------------------------------------------------- Gaussian spreading
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_gaussian_spreading_of_the_reactant(axis):
+    """A Gaussian bump of C on a uniform background, no flow, no reaction: the variance
+    grows at 2 D (fitted slope over steps 50 - 500, 1e-3)."""
+    n, D = 128, 0.05
+    shape = [1, 1, 1]
+    shape[2 - axis] = n
+    shape = tuple(shape)
+    s = np.arange(n).reshape(shape).astype(np.float64)
+    conc = 1.0 + 0.5 * np.exp(-((s - 64.0) ** 2) / (2 * 2.0 ** 2))
+    ones = np.ones(shape, np.float32)
+    var, times = [], []
+    with lbm.Lattice(np.zeros(shape, bool), lbm.Params(diffusivity=D, k_rate=0.0, sigma=0.0)) as L:
+        L.init_fields(ones, np.zeros(shape, np.float32), conc.astype(np.float32))
+        for t in range(50, 501, 50):
+            L.step(50)
+            c = L.get_state()[38:45].astype(np.float64).sum(axis=0).ravel() - 1.0
+            x = np.arange(n)
+            m = (c * x).sum() / c.sum()
+            var.append((c * (x - m) ** 2).sum() / c.sum())
+            times.append(t)
+    slope = np.polyfit(times, var, 1)[0]
+    assert abs(slope / (2 * D) - 1) < 1e-3, slope / (2 * D)
+
+
+# --------------------------------------------------------------------- wall reaction
+def _slowest_mode(n, k, D):
+    """Slowest eigenpair of the node-centred diffusion operator with a k C sink at both wall layers."""
+    A = np.zeros((n, n))
+    for j in range(n):
+        A[j, j] = -2 * D
+        if j > 0:
+            A[j, j - 1] = D
+        if j < n - 1:
+            A[j, j + 1] = D
+    A[0, 0] += D - k
+    A[-1, -1] += D - k
+    ev, vec = np.linalg.eigh(A)
+    return -ev[-1], np.abs(vec[:, -1])
+
+
+def test_wall_reaction_decays_at_the_robin_rate():
+    """A channel at rest between plates, the fluid layers next to them reactive (NN = 1),
+    C started in the slowest mode: m^C decays at D mu^2 with mu h tan(mu h) = k h / D,
+    h = L / 2 (2 %: the lattice puts the sink half a node off the wall) and at the
+    node-centred eigenvalue (0.5 %)."""
+    n, k, D = 64, 1e-3, 0.05
+    h = n / 2
+    lo, hi = 1e-9, math.pi / 2 - 1e-9
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid * math.tan(mid) < k * h / D:
+            lo = mid
+        else:
+            hi = mid
+    lam = D * (lo / h) ** 2
+    lam_fd, vec = _slowest_mode(n, k, D)
+    shape = (n + 2, 1, 1)
+    solid = np.zeros(shape, bool)
+    solid[0] = solid[-1] = True
+    # C of 1e-4: the reacted amount (r -> p at the walls) stays too small to change psi
+    conc = np.full(shape, 1e-4, np.float32)
+    conc[1:-1, 0, 0] = 1e-4 * vec / vec.max()
+    ones = np.ones(shape, np.float32)
+    with lbm.Lattice(solid, lbm.Params(diffusivity=D, k_rate=k, sigma=0.0)) as L:
+        L.init_fields(ones, np.zeros(shape, np.float32), conc)
+        L.step(500)
+        m0 = L.observables()["mass_c"]
+        L.step(2500)
+        m1 = L.observables()["mass_c"]
+    meas = math.log(m0 / m1) / 2500
+    assert abs(meas / lam - 1) < 0.02, meas / lam
+    assert abs(meas / lam_fd - 1) < 0.005, meas / lam_fd

@@ -371,3 +371,31 @@ def test_full_size_column_sampled_nodes():
         ref, _ = pw.update((int(x), int(y), int(z)))
         worst = max(worst, float(np.abs(post[:, z, y, x].astype(np.float64) - ref).max()))
     assert worst < TOL_STEP_POP, worst
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_reaction_balance_every_step(mode):
+    """Eq. reactive_boundary_condition / the balance the paper's mass analysis rests on:
+    every step the reacted amount (FP64 sum of delta) leaves the red mass and enters the
+    blue mass (and, in mode 0, leaves the reactant C), to the FP32 conservation of a node
+    update (a few ulps of rho per node: bound 2e-7 per fluid node)."""
+    shape = (24, 20, 16)
+    solid = synth.grf_mask(shape, 3, 0.5, 21)
+    p = lbm.Params(sigma=0.02, theta_deg=45.0, k_rate=0.05, reaction_mode=mode, xi=1.0)
+    nf = int((~solid).sum())
+    bound = 2e-7 * nf
+    with lbm.Lattice(solid, p) as L:
+        L.step(5)
+        prev = L.observables()
+        consumed_prev = L.reaction()[1]
+        for _ in range(15):
+            L.step(1)
+            ob = L.observables()
+            rate, consumed = L.reaction()
+            assert rate > 0.0
+            assert abs((consumed - consumed_prev) - rate) <= 1e-12 * max(1.0, consumed)
+            assert abs((ob["mass_r"] - prev["mass_r"]) + rate) <= bound, (ob["mass_r"] - prev["mass_r"], rate)
+            assert abs((ob["mass_p"] - prev["mass_p"]) - rate) <= bound, (ob["mass_p"] - prev["mass_p"], rate)
+            if mode == 0:
+                assert abs((ob["mass_c"] - prev["mass_c"]) + rate) <= bound, (ob["mass_c"] - prev["mass_c"], rate)
+            prev, consumed_prev = ob, consumed

@@ -10,7 +10,8 @@
 // own size, mask and parameters).  All their slots share one slot space:
 // instance k owns the fluid slots [slot_off, slot_off + nf) in lattice order and,
 // in column mode, the ghost slots [ghost, ghost + 2 * plane) (inlet plane, then
-// outlet plane).  Population p of global slot s sits at f[p * ns + s].  Every
+// outlet plane).  The populations of global slot s sit in the slot layout below
+// (pop_index: f^r_i and f^p_i of s adjacent, g_j at 2 Q ns + j ns + s).  Every
 // per-step kernel is one launch over all slots of all instances; a thread finds
 // its node (packed x | y << 10 | z << 20, or kNoNode) and its instance (the
 // per-slot instance array, absent for a single instance) and reads the

@@ -462,6 +462,8 @@ def run_native(args):
         "config": {"workload": wl.name, "lattice_xyz": [wl.shape[2], wl.shape[1], wl.shape[0]],
                    "mask": f"GRF shell |k|={wl.shell_k0}+-1, porosity {wl.porosity}, seed {wl.seed}",
                    "fluid_nodes": Nf, "porosity": round(Nf / N, 4),
+                   "wall_nodes": info["n_wall"], "wall_fraction_of_fluid": round(info["n_wall"] / Nf, 4),
+                   "boundary_solid_nodes": info["n_solid_bnd"],
                    "boundaries": "inlet/outlet in z" if wl.bc_z else "periodic",
                    "storage": ["fp32", "fp16 deviations"][head.storage],
                    "fluid_mlups": round(world * Nf * args.steps / (t_ms * 1e-3) / 1e6, 2),

@@ -105,6 +105,29 @@ def test_state_gradient_one_step():
     assert np.all(dth[fl] == 0.0)
 
 
+@pytest.mark.parametrize("shape", [(2, 7, 9), (3, 8, 6), (4, 5, 7)])
+def test_thin_columns_three_steps(shape):
+    """Columns two to four planes deep (the least a column takes), where every node sits
+    next to a ghost plane and populations leave at both ends: three steps with
+    checkpoints every two, dJ/df_0, dJ/dtheta and dJ/du_in against the FP64 autograd
+    reference (2e-4 of the largest entry)."""
+    solid, p, op, g, theta, f0 = _case(shape, 11 + shape[0])
+    with lbm.Lattice(solid, p, bc_z=1, theta=theta) as L:
+        L.set_state(f0)
+        J = L.adjoint_forward(3, 2)
+        dth, du, ds = L.adjoint_backward(want_state=True)
+    Jr, dthr, dur, dsr = _reference(g, op, f0, theta, 3, want_state=True)
+    assert abs(J - Jr) < 1e-5 * max(1.0, abs(Jr))
+    fl = g.fluid
+    scale = np.abs(dsr[:, fl]).max()
+    err = np.abs(ds.astype(np.float64) - dsr)[:, fl]
+    assert err.max() < 2e-4 * scale, (err.max(), scale)
+    sc = np.abs(dthr).max()
+    if sc > 0:
+        assert np.abs(dth - dthr).max() < 2e-4 * sc, (np.abs(dth - dthr).max(), sc)
+    assert abs(du - dur) < 2e-4 * abs(dur), (du, dur)
+
+
 def _reference_along(g, op, states, theta, nsteps):
     """FP64 adjoint linearised along a given trajectory (the GPU's own FP32 states)."""
     ts = A.TorchStep(g, op)

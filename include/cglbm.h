@@ -238,9 +238,10 @@ int lbm_set_inlet(lbm_ctx *ctx, double u_in, double c_in);
  * lbm_adjoint_forward advances the state by nsteps exactly as lbm_step does,
  * storing a checkpoint every checkpoint_every steps (<= 0: ceil(sqrt(nsteps))),
  * and returns J in *objective (may be NULL).  Device memory for about
- * nsteps / K + K + 3 population states (K = checkpoint spacing) is allocated on
- * first use and kept until lbm_destroy.  LBM_ENAN if Phi_in is zero or the
- * fluxes are not finite.
+ * nsteps / K + K + 2 population states (K = checkpoint spacing), with the
+ * density, normal and curvature fields of K states, is allocated on first use
+ * and kept until lbm_destroy.  LBM_ENAN if Phi_in is zero or the fluxes are not
+ * finite.
  *
  * lbm_adjoint_backward (valid until the state changes) recomputes each segment
  * from its checkpoint and runs the adjoint steps backwards.  Outputs, each

@@ -21,6 +21,7 @@ import numpy as np
 import pytest
 
 from oracle import cglbm as O
+from oracle.lattice import W19, W7
 from oracle.pointwise import PointwiseStep
 from paper_2608_15781_b300 import build, lbm, synth
 
@@ -335,19 +336,26 @@ def test_invalid_state_sizes_and_nan_detection():
 
 
 # --------------------------------------------------------------------- full size, sampled nodes
-def test_full_size_column_sampled_nodes():
-    """128 x 128 x 256 column (shell 8, porosity 0.5, seed 2) in the bench's launch configuration.
+@pytest.mark.parametrize("storage", [0, 1])
+def test_full_size_column_sampled_nodes(storage):
+    """128 x 128 x 256 column (shell 8, porosity 0.5, seed 2) in the bench's launch
+    configuration (main, colour-function and normal kernels with 128 threads,
+    programmatic launch, three field kernels), FP32 and FP16 storage.
 
     After 40 steps from a start with gas droplets, one more step is checked node
     by node on a sample (wall nodes, inlet and outlet planes, bulk) against the
-    per-node oracle evaluated on the downloaded pre-step state.
+    per-node oracle evaluated on the downloaded pre-step state: FP32 to 5e-7, FP16
+    within one FP16 spacing of the stored deviation (2^-10 |ref - reference
+    equilibrium| + 1e-6, and 5e-4 more on the planes that pull FP16-stored ghost
+    populations, as in the FP16 single-step test).
     """
     shape = (256, 128, 128)
     solid = synth.grf_mask(shape, 8, 0.5, 2, periodic_z=False)
-    p = lbm.Params(theta_deg=60.0, k_rate=5e-3, u_in=0.005, c_in=1.0, sigma=0.01)
+    p = lbm.Params(theta_deg=60.0, k_rate=5e-3, u_in=0.005, c_in=1.0, sigma=0.01, storage=storage)
     op = _oparams(p, 1)
     rr, rp = synth.droplet_fields(shape, (64, 64, 128), 20.0, inside_r=False)
     with lbm.Lattice(solid, p, bc_z=1) as L:
+        L.set_launch(dict(main=128, density=128, normal=128, pdl=1, fields=0))
         L.init_fields(rr, rp, np.ones(shape))
         L.step(40)
         pre = L.get_state()
@@ -366,11 +374,17 @@ def test_full_size_column_sampled_nodes():
     for grp in groups:
         idx = rng.choice(len(grp), size=min(12, len(grp)), replace=False)
         picked += [tuple(grp[i]) for i in idx]
+    ref_eq = np.concatenate([W19, np.zeros(19), W7]) if storage else None
     worst = 0.0
     for z, y, x in picked:
         ref, _ = pw.update((int(x), int(y), int(z)))
-        worst = max(worst, float(np.abs(post[:, z, y, x].astype(np.float64) - ref).max()))
-    assert worst < TOL_STEP_POP, worst
+        err = np.abs(post[:, z, y, x].astype(np.float64) - ref)
+        if storage == 0:
+            worst = max(worst, float(err.max()))
+        else:
+            bound = 2.0 ** -10 * np.abs(ref - ref_eq) + 1e-6 + (5e-4 if z in (0, shape[0] - 1) else 0.0)
+            worst = max(worst, float((err / bound).max()))
+    assert worst < (TOL_STEP_POP if storage == 0 else 1.0), worst
 
 
 @pytest.mark.parametrize("mode", [0, 1])

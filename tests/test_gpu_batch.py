@@ -89,3 +89,39 @@ def test_set_state_of_one_lattice_keeps_the_others():
         B.set_state(1, f)
         for k in range(len(solids)):
             assert np.abs(B.get_state(k) - keep[k]).max() == 0.0, k
+
+
+def test_full_batch_workload_sampled_nodes():
+    """The bench's batch of 64 columns (edges 48-96, 26 M nodes) in its launch
+    configuration: after 10 steps, one more step checked node by node against the
+    per-node oracle on the downloaded pre-step state of every eighth lattice (wall
+    nodes, bulk, inlet and outlet planes; 5e-7)."""
+    from oracle.pointwise import PointwiseStep
+    from paper_2608_15781_b300.configs import batched_workload
+
+    masks, params, bcs, edges = batched_workload()
+    rng = np.random.default_rng(5)
+    with lbm.Batch(masks, params, bc_z=bcs) as B:
+        B.set_launch(dict(main=128, density=128, normal=128, pdl=1, fields=0))
+        B.step(10)
+        ks = list(range(0, len(masks), 8))
+        pre = {k: B.get_state(k) for k in ks}
+        B.step(1)
+        post = {k: B.get_state(k) for k in ks}
+    worst = 0.0
+    for k in ks:
+        solid = masks[k]
+        pw = PointwiseStep(pre[k], solid, _oparams(params[k], bcs[k]))
+        fluid = ~solid
+        wall = np.zeros(solid.shape, bool)
+        for c in O.C19[:18]:
+            wall |= O.neighbor(solid, c, "clamp")
+        zs = np.argwhere(fluid)
+        groups = [np.argwhere(fluid & wall), np.argwhere(fluid & ~wall), zs[zs[:, 0] == 0],
+                  zs[zs[:, 0] == solid.shape[0] - 1]]
+        for grp in groups:
+            for i in rng.choice(len(grp), size=min(4, len(grp)), replace=False):
+                z, y, x = (int(v) for v in grp[i])
+                ref, _ = pw.update((x, y, z))
+                worst = max(worst, float(np.abs(post[k][:, z, y, x].astype(np.float64) - ref).max()))
+    assert worst < 5e-7, worst

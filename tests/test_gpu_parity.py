@@ -413,3 +413,42 @@ def test_reaction_balance_every_step(mode):
             if mode == 0:
                 assert abs((ob["mass_c"] - prev["mass_c"]) + rate) <= bound, (ob["mass_c"] - prev["mass_c"], rate)
             prev, consumed_prev = ob, consumed
+
+
+def test_paper_mode_workload_sampled_nodes():
+    """The 128^3 paper-mode box (shell 6, porosity 0.5, seed 6, periodic; sigma 0.3, body
+    force 3.616e-5 along x, xi = 1, one nucleation site per 64^3 block from
+    analysis.nucleation_sites) in the bench's launch configuration, from a start with
+    gas droplets: after 40 steps one more step checked on sampled nodes (the sites, wall
+    nodes, bulk) against the per-node oracle (5e-7)."""
+    from paper_2608_15781_b300 import analysis
+    from paper_2608_15781_b300.configs import WORKLOADS
+
+    wl = WORKLOADS["paper128"]
+    solid = wl.mask()
+    sites = analysis.nucleation_sites(solid, block=64, seed=0)
+    p = wl.params
+    shape = solid.shape
+    rr, rp = synth.droplet_fields(shape, (64, 64, 64), 16.0, inside_r=False)
+    with lbm.Lattice(solid, p, reactive=sites) as L:
+        L.set_launch(dict(main=128, density=128, normal=128, pdl=1, fields=0))
+        L.init_fields(rr, rp, np.ones(shape))
+        L.step(40)
+        pre = L.get_state()
+        L.step(1)
+        post = L.get_state()
+    pw = PointwiseStep(pre, solid, _oparams(p, 0), reactive=sites)
+    rng = np.random.default_rng(13)
+    fluid = ~solid
+    wall = np.zeros(shape, bool)
+    for c in O.C19[:18]:
+        wall |= O.neighbor(solid, c, "periodic")
+    picked = [tuple(v) for v in np.argwhere(sites)]
+    for grp in (np.argwhere(fluid & wall), np.argwhere(fluid & ~wall)):
+        idx = rng.choice(len(grp), size=min(16, len(grp)), replace=False)
+        picked += [tuple(grp[i]) for i in idx]
+    worst = 0.0
+    for z, y, x in picked:
+        ref, _ = pw.update((int(x), int(y), int(z)))
+        worst = max(worst, float(np.abs(post[:, z, y, x].astype(np.float64) - ref).max()))
+    assert worst < TOL_STEP_POP, worst

@@ -452,3 +452,47 @@ def test_paper_mode_workload_sampled_nodes():
         ref, _ = pw.update((int(x), int(y), int(z)))
         worst = max(worst, float(np.abs(post[:, z, y, x].astype(np.float64) - ref).max()))
     assert worst < TOL_STEP_POP, worst
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_precision_workload_sampled_nodes(storage):
+    """The 256^3 periodic precision box (shell 12, porosity 0.5, seed 3) in FP32 and FP16
+    storage, bench launch configuration: after 30 steps with reaction from a start with
+    gas droplets, one more step checked on sampled nodes against the per-node oracle
+    (FP32 5e-7; FP16 within one FP16 spacing of the stored deviation)."""
+    import dataclasses
+
+    from paper_2608_15781_b300.configs import WORKLOADS
+
+    wl = WORKLOADS["periodic256"]
+    solid = wl.mask()
+    p = dataclasses.replace(wl.params, storage=storage)
+    shape = solid.shape
+    rr, rp = synth.droplet_fields(shape, (128, 128, 128), 24.0, inside_r=False)
+    with lbm.Lattice(solid, p) as L:
+        L.set_launch(dict(main=128, density=128, normal=128, pdl=1, fields=0))
+        L.init_fields(rr, rp, np.ones(shape))
+        L.step(30)
+        pre = L.get_state()
+        L.step(1)
+        post = L.get_state()
+    pw = PointwiseStep(pre, solid, _oparams(p, 0))
+    rng = np.random.default_rng(17)
+    fluid = ~solid
+    wall = np.zeros(shape, bool)
+    for c in O.C19[:18]:
+        wall |= O.neighbor(solid, c, "periodic")
+    picked = []
+    for grp in (np.argwhere(fluid & wall), np.argwhere(fluid & ~wall)):
+        idx = rng.choice(len(grp), size=min(24, len(grp)), replace=False)
+        picked += [tuple(grp[i]) for i in idx]
+    ref_eq = np.concatenate([W19, np.zeros(19), W7])
+    worst = 0.0
+    for z, y, x in picked:
+        ref, _ = pw.update((int(x), int(y), int(z)))
+        err = np.abs(post[:, z, y, x].astype(np.float64) - ref)
+        if storage == 0:
+            worst = max(worst, float(err.max()))
+        else:
+            worst = max(worst, float((err / (2.0 ** -10 * np.abs(ref - ref_eq) + 1e-6)).max()))
+    assert worst < (TOL_STEP_POP if storage == 0 else 1.0), worst

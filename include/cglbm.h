@@ -94,7 +94,8 @@ typedef struct {
   int32_t storage;    /* population storage: 0 = FP32; 1 = FP16 deviations from the resting
                          reactant equilibrium (f^r - w, f^p, g - w, scaled by 2^12, so
                          deviations up to 16 in magnitude are representable), unbiased
-                         stochastic rounding, FP32 arithmetic                                 */
+                         stochastic rounding whose bits follow the step counter (reset with
+                         it by lbm_init_fields / lbm_set_state), FP32 arithmetic              */
   void *cuda_stream;  /* cudaStream_t to launch on (borrowed); NULL = legacy default stream  */
 } lbm_params;
 

@@ -503,6 +503,7 @@ int reset_after_state(Batch &b) {
     CK(cudaGetLastError());
   }
   CK(cudaMemsetAsync(b.acc, 0, 4 * sizeof(double) * b.n, b.stream));
+  CK(cudaMemsetAsync(b.rstep, 0, 2 * sizeof(uint32_t), b.stream));   // FP16 rounding bits restart with the steps
   int rc = launch_observables(b);
   if (rc) return rc;
   std::vector<double> hobs(8 * (size_t)b.n);

@@ -43,8 +43,12 @@ def test_reaction_async_matches_synchronous_read():
     assert np.all(np.diff(r[:, 1]) >= 0) and r[-1, 1] > 0
 
 
-def test_set_inlet_and_wetting_equal_a_fresh_context():
+@pytest.mark.parametrize("storage", [0, 1])
+def test_set_inlet_and_wetting_equal_a_fresh_context(storage):
+    """Also with FP16 storage: its rounding bits restart with the step counter, so a
+    re-initialised context rounds exactly as a fresh one."""
     solid, p = _column()
+    p = dataclasses.replace(p, storage=storage)
     rng = np.random.default_rng(1)
     theta = rng.uniform(30, 110, solid.shape).astype(np.float32)
     q = dataclasses.replace(p, u_in=0.009, c_in=0.6)

@@ -161,8 +161,9 @@ def test_precision_crop_against_fp64(storage):
     FP16 storage: within 3e-4 (measured up to 1.9e-4, 2.5e-4 with other rounding
     seeds); the stochastic rounding is unbiased, and the error is the trajectory's
     response to the rounding noise (its sign and size change with the seed of the
-    rounding bits).  The stated 1e-4 budget of the reduced-precision forms is met at
-    some sampled steps, not at all of them."""
+    rounding bits).  The stated 1e-4 budget of the reduced-precision forms is met up
+    to step 2500, not at all later samples: see the next test for why no inexact run
+    can be held to it on this workload."""
     obs, vel = _read_crop_reference()
     solid = synth.grf_mask((256, 256, 256), 12, 0.5, 3, periodic_z=True)[:64, :64, :64].copy()
     p = lbm.Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=1e-3, diffusivity=0.05, c_init=1.0,
@@ -188,6 +189,43 @@ def test_precision_crop_against_fp64(storage):
     assert max(dc) < tol and max(ds) < tol, (dc, ds)
     if storage == 0:
         assert du.max() < 0.02 * umax, du.max()
+
+
+def _crop_conversion_errors(storage, draw=None):
+    """Largest |conversion - FP64| over the crop reference's samples, from the reference's
+    start or from one multiplied by 1 + 1e-6 N(0, 1) per f^r_i (seed 100 + draw)."""
+    obs, _ = _read_crop_reference()
+    solid = synth.grf_mask((256, 256, 256), 12, 0.5, 3, periodic_z=True)[:64, :64, :64].copy()
+    p = lbm.Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=1e-3, diffusivity=0.05, c_init=1.0,
+                   storage=storage)
+    dc, done = [], 0
+    with lbm.Lattice(solid, p, bc_z=0) as L:
+        if draw is not None:
+            f = L.get_state().astype(np.float64)
+            f[0:19] *= 1.0 + 1e-6 * np.random.default_rng(100 + draw).standard_normal(f[0:19].shape)
+            L.set_state(f.astype(np.float32))
+        for row in obs:
+            L.step(int(row[0]) - done)
+            done = int(row[0])
+            dc.append(abs(L.observables()["conversion"] - row[1]))
+    return max(dc)
+
+
+def test_precision_crop_conversion_is_set_by_fluctuations():
+    """The crop starts as a uniform liquid that the wall reaction supersaturates with
+    product; where and when the gas phase separates is decided by fluctuations.  The
+    noiseless runs (FP64, FP32 with its deterministic rounding) follow one history; a
+    relative 1e-6 change of the start (three draws) moves FP32's conversion away from
+    FP64's by up to 1.3e-4 (measured 8e-6, 8.6e-5, 1.3e-4), against 8e-7 without it; the
+    larger deviations have the sign of the FP16 runs' (lower conversion after step 2500),
+    whose rounding noise acts as a fluctuation at every step.  So the FP16 error
+    (1.9e-4) is of the size of the trajectory's own sensitivity, and the check is that it
+    stays within 3x of the largest FP32 deviation from a perturbed start."""
+    fp32 = [_crop_conversion_errors(0, d) for d in range(3)]
+    fp16 = _crop_conversion_errors(1)
+    print(f"\nFP32 from 1e-6 perturbed starts: {', '.join(f'{e:.2e}' for e in fp32)}; FP16: {fp16:.2e}")
+    assert max(fp32) > 3e-5, fp32          # the unperturbed FP32 run is within 1e-5 (previous test)
+    assert fp16 < 3.0 * max(fp32), (fp16, fp32)
 
 
 def test_fp16_storage_conserves_mass_without_reaction():

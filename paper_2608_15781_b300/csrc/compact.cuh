@@ -288,18 +288,28 @@ __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+// The same in two halves, for kernels that first load what no step writes (slot
+// map, node words, link words, solid normals, boundary lists): those loads are
+// issued before the wait, so a block resident before its predecessor finishes
+// has them in flight while it waits.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// pull of the 45 (38) populations of fluid slot t at (x, y, z), halfway bounce-back
-// where the source is solid (gidx < 0)
-template <typename T>
-__device__ __forceinline__ void pull_compact(int ns_, const StepParams &P, const T *__restrict__ fin,
-                                             const int *__restrict__ gidx, const PullOffsets &O, unsigned t,
-                                             float (&fr)[Q], float (&fp)[Q], float (&g)[Q7]) {
-  const unsigned ns = (unsigned)ns_;
-  int src[Q];
+// source slots of the pull of fluid slot t at (x, y, z): the slot of x - c_i, or
+// -1 where that node is solid (halfway bounce-back); the rest population's is t
+__device__ __forceinline__ void pull_sources(const int *__restrict__ gidx, const PullOffsets &O, unsigned t,
+                                             int (&src)[Q]) {
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) src[i] = __ldg(gidx + O.src(CX[i], CY[i], CZ[i]));
   src[Q - 1] = (int)t;
+}
+
+// pull of the 45 (38) populations of fluid slot t from its source slots
+template <typename T>
+__device__ __forceinline__ void pull_compact(int ns_, const StepParams &P, const T *__restrict__ fin,
+                                             const int (&src)[Q], unsigned t, float (&fr)[Q], float (&fp)[Q],
+                                             float (&g)[Q7]) {
+  const unsigned ns = (unsigned)ns_;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const bool bb = src[i] < 0;
@@ -333,7 +343,7 @@ template <typename T, int BLOCK, bool BATCH>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, const __grid_constant__ Inst single,
                                                      const T *__restrict__ f, const int *__restrict__ gidx,
                                                      float *__restrict__ rhoN) {
-  pdl_begin();
+  pdl_trigger();
   // the blocks walk the slots from the end: the first ones read what the main kernel
   // of the previous step wrote last, which is still in L2 (67.5 -> 65.1 us on the
   // 128x128x256 column)
@@ -346,12 +356,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, cons
   unpack(pk, x, y, z);
   PullOffsets O;
   O.init(I.L, x, y, z);
-  const int *gi = gidx + (BATCH ? I.gidx_off : 0);
   const unsigned ns = (unsigned)S.ns;
+  int src[Q];
+  pull_sources(gidx + (BATCH ? I.gidx_off : 0), O, t, src);
+  pdl_wait();
   float rr = 0.f, rp = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const int si = i == Q - 1 ? (int)t : __ldg(gi + O.src(CX[i], CY[i], CZ[i]));
+    const int si = src[i];
     const bool bb = si < 0;
     const unsigned s = bb ? t : (unsigned)si;
     const unsigned pr = bb ? (unsigned)OPP[i] : (unsigned)i;
@@ -368,7 +380,7 @@ template <int BLOCK, bool BATCH>
 __global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const __grid_constant__ Inst single,
                                                     const float *__restrict__ rhoN, const uint32_t *__restrict__ link,
                                                     const float4 *__restrict__ ns, float4 *__restrict__ nrm) {
-  pdl_begin();
+  pdl_trigger();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)S.nslots) return;
   const uint32_t pk = S.node[t];
@@ -386,6 +398,7 @@ __global__ void __launch_bounds__(BLOCK) k_normal_c(Slots S, const __grid_consta
   const int noff = BATCH ? I.node_off : 0;
   const uint32_t lk = __ldg(link + noff + node);
   const float4 s = __ldg(ns + noff + node);
+  pdl_wait();
   float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) {
@@ -409,7 +422,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(128) k_color_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
                                 const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
                                 const uint32_t *__restrict__ list_link, float *__restrict__ rhoN) {
-  pdl_begin();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const Inst &I = BATCH ? inst[kid[t]] : single;
@@ -419,6 +432,7 @@ __global__ void __launch_bounds__(128) k_color_solid_c(const Inst *__restrict__ 
   StencilOffsets St;
   St.init(I.L, x, y, z);
   float *rn = rhoN + I.node_off;
+  pdl_wait();
   float v[Q - 1];
 #pragma unroll
   for (int i = 0; i < Q - 1; ++i) v[i] = rn[St.nb(CX[i], CY[i], CZ[i])];
@@ -436,7 +450,7 @@ template <bool BATCH>
 __global__ void k_normal_solid_c(const Inst *__restrict__ inst, const __grid_constant__ Inst single,
                                  const uint32_t *__restrict__ list, const uint16_t *__restrict__ kid, int count,
                                  const uint32_t *__restrict__ list_link, float4 *__restrict__ nrm) {
-  pdl_begin();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const Inst &I = BATCH ? inst[kid[t]] : single;
@@ -445,6 +459,7 @@ __global__ void k_normal_solid_c(const Inst *__restrict__ inst, const __grid_con
   const uint32_t lk = list_link[t];   // the entry's link word, loaded beside it
   StencilOffsets St;
   St.init(I.L, x, y, z);
+  pdl_wait();
   float4 *nn = nrm + I.node_off;
   float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
@@ -740,8 +755,27 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
                                                                int slot, uint32_t *__restrict__ rstep,
                                                                float *__restrict__ dbg_H,
                                                                float *__restrict__ dbg_delta) {
-  pdl_begin();
+  pdl_trigger();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = BATCH ? slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1) : 0;
+  const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
+  // FP16 storage: the source slots and the link word are loaded before the wait
+  // (step 223.9 -> 221.4 us on the 128x128x256 column); FP32 storage loads them after
+  // the curvature, as holding the 18 sources across it spills at 64 registers (the
+  // step 0.6 % slower)
+  constexpr bool EARLY = std::is_same<T, __half>::value;
+  int src[Q];
+  uint32_t lk = 0;
+  if (EARLY && pk != kNoNode) {
+    const Inst &I = inst_of<BATCH>(S, single, k);
+    int x, y, z;
+    unpack(pk, x, y, z);
+    PullOffsets O;
+    O.init(I.L, x, y, z);
+    pull_sources(gidx + (BATCH ? I.gidx_off : 0), O, t, src);
+    lk = __ldg(link + (BATCH ? I.node_off : 0) + nidx(I.L, x, y, z));
+  }
+  pdl_wait();
   // step counter of the FP16 rounding: read from this step's slot, the next value
   // written to the other one (read by the next step's main kernel)
   const uint32_t step = rstep[slot];
@@ -754,8 +788,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     }
   }
   double dsum[1] = {0.0};
-  const int k = BATCH ? slot_instance(S, t < (unsigned)S.nslots ? t : (unsigned)S.nslots - 1) : 0;
-  const uint32_t pk = t < (unsigned)S.nslots ? S.node[t] : kNoNode;
   if (pk != kNoNode) {
     const Inst &I = inst_of<BATCH>(S, single, k);
     int x, y, z;
@@ -765,15 +797,18 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     const unsigned node = St.own;
     const int noff = BATCH ? I.node_off : 0;
     const float4 *nn = nrm + noff;
-    const uint32_t lk = link[noff + node];
+    if (!EARLY) lk = link[noff + node];
     const float4 nme = nn[node];
     constexpr bool LEAN = std::is_same<T, __half>::value;
     const float H =
         nme.w >= GRAD_EPS ? curvature<LEAN>(nme, [&](int i) { return nn[St.nb(CX[i], CY[i], CZ[i])]; }) : 0.f;
-    PullOffsets O;
-    O.init(I.L, x, y, z);
+    if (!EARLY) {
+      PullOffsets O;
+      O.init(I.L, x, y, z);
+      pull_sources(gidx + (BATCH ? I.gidx_off : 0), O, t, src);
+    }
     float fr[Q], fp[Q], g[Q7];
-    pull_compact<T>(S.ns, I.P, fin, gidx + (BATCH ? I.gidx_off : 0), O, t, fr, fp, g);
+    pull_compact<T>(S.ns, I.P, fin, src, t, fr, fp, g);
     const float delta = collide_node<LEAN>(I.P, lk, fr, fp, g, nme, H);
     const unsigned ns = (unsigned)S.ns;
     // FP16 rounding bits (unused for FP32); fr + fp of the rest population sums rho

@@ -132,7 +132,7 @@ int dalloc(Batch &b, void **p, size_t bytes) {
   return LBM_OK;
 }
 
-dim3 node_block() { return dim3(32, 4, 1); }
+dim3 node_block() { return dim3(kGeomBX, kGeomBY, 1); }   // k_geom stages its tile for this shape
 dim3 node_grid(const Lattice &L) { return dim3((L.nx + 31) / 32, (L.ny + 3) / 4, L.nz); }
 
 void prof_begin(Batch &b, int kind, cudaStream_t st) {

@@ -222,12 +222,31 @@ __device__ __forceinline__ bool solid_at(const Lattice &L, const uint8_t *__rest
 // ns[node].w of a wall node holds its contact angle theta in radians: the
 // uniform value theta_rad, or the D3Q19-weighted mean of a per-solid-node field
 // (k_wall_theta).  k_geom writes the uniform value.
-__global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8_t *__restrict__ reactive,
-                       float theta_rad, uint32_t *__restrict__ link, float4 *__restrict__ ns) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+// It runs in blocks of kGeomBX x kGeomBY nodes of one z-plane (node_block()): the block
+// first stages the mask of its nodes and of everything within kGeomH nodes of them (the
+// reach of the solid-normal stencil) in shared memory, with solid_at's periodic and
+// clamped-ghost rules applied once per staged byte, so the 18- and 92-point stencils
+// below read shared memory only.
+constexpr int kGeomBX = 32, kGeomBY = 4, kGeomH = 2;
+constexpr int kGeomTX = kGeomBX + 2 * kGeomH, kGeomTY = kGeomBY + 2 * kGeomH, kGeomTZ = 1 + 2 * kGeomH;
+
+__global__ void __launch_bounds__(kGeomBX * kGeomBY) k_geom(Lattice L, const uint8_t *__restrict__ solid,
+                                                            const uint8_t *__restrict__ reactive, float theta_rad,
+                                                            uint32_t *__restrict__ link, float4 *__restrict__ ns) {
+  __shared__ uint8_t tile[kGeomTZ][kGeomTY][kGeomTX];
+  const int x0 = blockIdx.x * kGeomBX, y0 = blockIdx.y * kGeomBY, z = blockIdx.z;
+  for (int q = threadIdx.y * kGeomBX + threadIdx.x; q < kGeomTZ * kGeomTY * kGeomTX; q += kGeomBX * kGeomBY) {
+    const int tx = q % kGeomTX, ty = (q / kGeomTX) % kGeomTY, tz = q / (kGeomTX * kGeomTY);
+    (&tile[0][0][0])[q] = solid_at(L, solid, x0 + tx - kGeomH, y0 + ty - kGeomH, z + tz - kGeomH) ? 1 : 0;
+  }
+  __syncthreads();
+  const int x = x0 + (int)threadIdx.x;
+  const int y = y0 + (int)threadIdx.y;
   if (x >= L.nx || y >= L.ny) return;
+  // the mask at (x + dx, y + dy, z + dz), |d| <= kGeomH, by solid_at's rules
+  auto sol = [&](int dx, int dy, int dz) {
+    return tile[dz + kGeomH][(int)threadIdx.y + dy + kGeomH][(int)threadIdx.x + dx + kGeomH] != 0;
+  };
   const long long node = nidx(L, x, y, z);
   uint32_t bits = 0;
   float4 nsv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -236,19 +255,19 @@ __global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8
     // solid-colour and solid-normal averages
     bits = BIT_SOLID;
     for (int i = 0; i < Q - 1; ++i)
-      if (!solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i])) bits |= BIT_SOLID_BND | (1u << i);
+      if (!sol(CX[i], CY[i], CZ[i])) bits |= BIT_SOLID_BND | (1u << i);
   } else {
     // bounce-back links: the pull source x - c_i is solid (column ghosts are fluid)
     for (int i = 0; i < Q - 1; ++i) {
       const int sz = z - CZ[i];
       if (L.bc_z == 1 && (sz < 0 || sz >= L.nz)) continue;
-      if (solid_at(L, solid, x - CX[i], y - CY[i], sz)) bits |= 1u << i;
+      if (sol(-CX[i], -CY[i], -CZ[i])) bits |= 1u << i;
     }
     bool wall = false;
-    for (int i = 0; i < Q - 1; ++i) wall |= solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i]);
+    for (int i = 0; i < Q - 1; ++i) wall |= sol(CX[i], CY[i], CZ[i]);
     // Eq. nearest_solid_neighbors
     int nn = 0;
-    for (int i = 0; i < 6; ++i) nn += solid_at(L, solid, x + CX[i], y + CY[i], z + CZ[i]) ? 1 : 0;
+    for (int i = 0; i < 6; ++i) nn += sol(CX[i], CY[i], CZ[i]) ? 1 : 0;
     bits |= (uint32_t)nn << NN_SHIFT;
     const bool r = reactive ? (reactive[node] != 0) : (nn >= 1);
     if (r) bits |= BIT_REACTIVE;
@@ -261,7 +280,7 @@ __global__ void k_geom(Lattice L, const uint8_t *__restrict__ solid, const uint8
           for (int ex = -2; ex <= 2; ++ex) {
             const float w = omega8(ex * ex + ey * ey + ez * ez);
             if (w == 0.f) continue;
-            if (solid_at(L, solid, x + ex, y + ey, z + ez)) {
+            if (sol(ex, ey, ez)) {
               sx += w * ex;
               sy += w * ey;
               sz += w * ez;

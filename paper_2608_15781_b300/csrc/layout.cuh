@@ -58,45 +58,65 @@ __global__ void __launch_bounds__(kLayoutBlock) k_layout_count(long long n, cons
   }
 }
 
-// exclusive prefix of cf and cb over nb blocks (in place); totals of cf, cb, cw into tot[0..2]
-__global__ void __launch_bounds__(1024) k_layout_scan(int nb, int *__restrict__ cf, int *__restrict__ cb,
-                                                      const int *__restrict__ cw, long long *__restrict__ tot) {
-  __shared__ long long sf[1024], sb[1024];
-  __shared__ long long carry_f, carry_b, sum_w;
-  if (threadIdx.x == 0) {
-    carry_f = carry_b = sum_w = 0;
+// exclusive prefix of cf and cb over nb blocks (in place); totals of cf, cb, cw into tot[0..2].
+// One block of 1024 threads: thread j sums its own run of ceil(nb / 1024) consecutive
+// entries, the block scans the 1024 run sums, and each thread rewrites its run from
+// its run's offset.
+__device__ __forceinline__ long long block_exclusive_scan_1024(long long v, long long &total) {
+  __shared__ long long wsum[32];
+  __shared__ long long wtot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const long long w = wsum[lane];
+    long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    wsum[lane] = wi - w;   // exclusive prefix of the warp sums
+    if (lane == 31) wtot = wi;
   }
   __syncthreads();
-  for (int base = 0; base < nb; base += 1024) {
-    const int i = base + threadIdx.x;
-    const long long vf = i < nb ? cf[i] : 0, vb = i < nb ? cb[i] : 0;
-    sf[threadIdx.x] = vf;
-    sb[threadIdx.x] = vb;
-    if (i < nb) atomicAdd((unsigned long long *)&sum_w, (unsigned long long)cw[i]);
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
-      const long long af = threadIdx.x >= o ? sf[threadIdx.x - o] : 0;
-      const long long ab = threadIdx.x >= o ? sb[threadIdx.x - o] : 0;
-      __syncthreads();
-      sf[threadIdx.x] += af;
-      sb[threadIdx.x] += ab;
-      __syncthreads();
-    }
-    if (i < nb) {
-      cf[i] = (int)(carry_f + sf[threadIdx.x] - vf);
-      cb[i] = (int)(carry_b + sb[threadIdx.x] - vb);
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) {
-      carry_f += sf[1023];
-      carry_b += sb[1023];
-    }
-    __syncthreads();
+  const long long r = wsum[warp] + incl - v;
+  total = wtot;
+  __syncthreads();   // wsum and wtot may be reused by the next call
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_layout_scan(int nb, int *__restrict__ cf, int *__restrict__ cb,
+                                                      const int *__restrict__ cw, long long *__restrict__ tot) {
+  const int run = (nb + 1023) / 1024;
+  const int i0 = min(nb, (int)threadIdx.x * run), i1 = min(nb, i0 + run);
+  long long sf = 0, sb = 0, sw = 0;
+  for (int i = i0; i < i1; ++i) {
+    sf += cf[i];
+    sb += cb[i];
+    sw += cw[i];
+  }
+  long long tf, tb, tw;
+  long long of = block_exclusive_scan_1024(sf, tf);
+  long long ob = block_exclusive_scan_1024(sb, tb);
+  (void)block_exclusive_scan_1024(sw, tw);
+  for (int i = i0; i < i1; ++i) {
+    const int vf = cf[i], vb = cb[i];
+    cf[i] = (int)of;
+    cb[i] = (int)ob;
+    of += vf;
+    ob += vb;
   }
   if (threadIdx.x == 0) {
-    tot[0] = carry_f;
-    tot[1] = carry_b;
-    tot[2] = sum_w;
+    tot[0] = tf;
+    tot[1] = tb;
+    tot[2] = tw;
   }
 }
 

@@ -150,8 +150,8 @@ int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
 int lbm_reaction(lbm_ctx *ctx, double *rate, double *consumed);
 
 /* The same two values without synchronising: enqueues on the context's stream
- * copies of the last step's sum of delta into dst[0] and the cumulative sum into
- * dst[1] (host memory; page-locked memory keeps the copy asynchronous).  dst must
+ * one 16-byte copy of the last step's sum of delta into dst[0] and the cumulative
+ * sum into dst[1] (host memory; page-locked memory keeps the copy asynchronous).  dst must
  * stay valid until the copies have run, i.e. until the next synchronising call on
  * the context or a synchronisation of its stream.  Call it before the next
  * lbm_step (the per-step slot is reused two steps later).  LBM_EINVAL before the

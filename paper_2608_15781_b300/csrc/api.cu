@@ -265,27 +265,30 @@ void launch_step_kernel(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned b
   launch_step_kernel_smem(pdl, k, grid, block, 0, st, args...);
 }
 
+// acc: the reaction-sum pairs that the step with parity slot accumulates into (its
+// colour-function pass sets them up), or null where nobody reads them
 template <typename T, bool BT>
-void launch_density_t(const Batch &b, cudaStream_t st, const void *fin) {
+void launch_density_t(const Batch &b, cudaStream_t st, const void *fin, double *acc, int slot) {
   const Slots S = slots(b);
   const Inst &I = b.h[0].d;
+  const T *f = (const T *)fin;
   switch (b.dens_block) {
     case 128:
-      k_density_c<T, 128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, (const T *)fin, b.gidx, b.rhoN);
+      k_density_c<T, 128, BT><<<(S.nslots + 127) / 128, 128, 0, st>>>(S, I, f, b.gidx, b.rhoN, acc, b.n, slot);
       break;
     case 512:
-      k_density_c<T, 512, BT><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, I, (const T *)fin, b.gidx, b.rhoN);
+      k_density_c<T, 512, BT><<<(S.nslots + 511) / 512, 512, 0, st>>>(S, I, f, b.gidx, b.rhoN, acc, b.n, slot);
       break;
     default:
-      k_density_c<T, 256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, (const T *)fin, b.gidx, b.rhoN);
+      k_density_c<T, 256, BT><<<(S.nslots + 255) / 256, 256, 0, st>>>(S, I, f, b.gidx, b.rhoN, acc, b.n, slot);
   }
 }
 template <typename T>
-void launch_density(const Batch &b, cudaStream_t st, const void *fin) {
+void launch_density(const Batch &b, cudaStream_t st, const void *fin, double *acc = nullptr, int slot = 0) {
   if (b.n > 1)
-    launch_density_t<T, true>(b, st, fin);
+    launch_density_t<T, true>(b, st, fin, acc, slot);
   else
-    launch_density_t<T, false>(b, st, fin);
+    launch_density_t<T, false>(b, st, fin, acc, slot);
 }
 
 template <bool BT>
@@ -412,7 +415,7 @@ void enqueue_step(Batch &b, cudaStream_t st, const void *fin, void *fout, int sl
   with_storage(b, [&](auto *tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
     pb(0);
-    launch_density<T>(b, st, fin);
+    launch_density<T>(b, st, fin, acc ? acc : b.acc, slot);
     pe();
     if (b.fields) {
       pb(6);
@@ -562,8 +565,9 @@ int fill_obs(Batch &b, lbm_obs *out, int count) {
     o.mass_r = h[0];
     o.mass_p = h[1];
     o.mass_c = h[2];
-    o.consumed = a[0];
-    o.rate = b.step > 0 ? a[2 + ((b.step - 1) & 1)] : 0.0;
+    const int s = (int)((b.step - 1) & 1);   // parity of the last step
+    o.consumed = b.step > 0 ? a[2 * s + 1] : 0.0;
+    o.rate = b.step > 0 ? a[2 * s] : 0.0;
     o.gas_saturation = h[3] / (double)b.h[k].n_fluid;
     o.flux_in = h[4];
     o.flux_out = h[5];
@@ -1508,8 +1512,9 @@ int lbm_reaction(lbm_ctx *c, double *rate, double *consumed) {
   double a[4];
   CK(cudaMemcpyAsync(a, b.acc, sizeof(a), cudaMemcpyDeviceToHost, b.stream));
   CK(cudaStreamSynchronize(b.stream));
-  if (rate) *rate = b.step > 0 ? a[2 + ((b.step - 1) & 1)] : 0.0;
-  if (consumed) *consumed = a[0];
+  const int s = (int)((b.step - 1) & 1);   // parity of the last step
+  if (rate) *rate = b.step > 0 ? a[2 * s] : 0.0;
+  if (consumed) *consumed = b.step > 0 ? a[2 * s + 1] : 0.0;
   return LBM_OK;
 }
 
@@ -1519,8 +1524,8 @@ int lbm_reaction_async(lbm_ctx *c, double *dst) {
   if (b.sticky) return b.sticky;
   if (b.step < 1) return LBM_EINVAL;
   cudaSetDevice(b.device);
-  CK(cudaMemcpyAsync(dst, b.acc + 2 + ((b.step - 1) & 1), sizeof(double), cudaMemcpyDeviceToHost, b.stream));
-  CK(cudaMemcpyAsync(dst + 1, b.acc, sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  // the last step's pair (its sum, the cumulative sum): one 16-byte copy
+  CK(cudaMemcpyAsync(dst, b.acc + 2 * ((b.step - 1) & 1), 2 * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   return LBM_OK;
 }
 

@@ -244,8 +244,11 @@ __device__ __forceinline__ void block_accumulate_inst(double (&v)[NV], int k, do
   }
 }
 
-// block sum of the reaction amounts into acc[4k] (cumulative) and acc[4k + 2 + slot]
-// (this step) of the threads' instance k (per thread when the block spans instances)
+// Reaction sums of instance k: acc[4k + 2 slot] = sum of delta over the step with
+// parity slot, acc[4k + 2 slot + 1] = cumulative sum after it (the pair is adjacent, so
+// one 16-byte copy reads both).  The step's colour-function pass sets the pair to (0,
+// cumulative sum after the previous step), see k_density_c; the main kernel adds
+// each block's sum to both (per thread when the block spans instances).
 template <bool BATCH>
 __device__ __forceinline__ void block_delta_inst(double d, int k, double *acc, int slot) {
   __shared__ double red[32];
@@ -267,13 +270,13 @@ __device__ __forceinline__ void block_delta_inst(double d, int k, double *acc, i
       double s = lane < nw ? red[lane] : 0.0;
       s = warp_sum(s);
       if (lane == 0 && s != 0.0) {
-        atomicAdd(acc + 4 * k0, s);
-        atomicAdd(acc + 4 * k0 + 2 + slot, s);
+        atomicAdd(acc + 4 * k0 + 2 * slot, s);
+        atomicAdd(acc + 4 * k0 + 2 * slot + 1, s);
       }
     }
   } else if (d != 0.0) {
-    atomicAdd(acc + 4 * k, d);
-    atomicAdd(acc + 4 * k + 2 + slot, d);
+    atomicAdd(acc + 4 * k + 2 * slot, d);
+    atomicAdd(acc + 4 * k + 2 * slot + 1, d);
   }
 }
 
@@ -342,8 +345,20 @@ __device__ __forceinline__ const Inst &inst_of(const Slots &S, const Inst &singl
 template <typename T, int BLOCK, bool BATCH>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, const __grid_constant__ Inst single,
                                                      const T *__restrict__ f, const int *__restrict__ gidx,
-                                                     float *__restrict__ rhoN) {
+                                                     float *__restrict__ rhoN, double *__restrict__ acc, int n_inst,
+                                                     int slot) {
   pdl_trigger();
+  // The reaction-sum pairs of this step (block_delta_inst) are set up here: the
+  // colour-function pass is the step's first kernel, launched after the previous step
+  // has completed, and the main kernel starts only after it has.  A batch sets them
+  // up in its first block, one instance per thread; one lattice, at the end of slot
+  // 0's thread (the same code at the start of the kernel cost the FP16 pass 0.8 us).
+  if (BATCH && acc && blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
+      acc[4 * k + 2 * slot] = 0.0;
+      acc[4 * k + 2 * slot + 1] = acc[4 * k + 2 * (slot ^ 1) + 1];
+    }
+  }
   // the blocks walk the slots from the end: the first ones read what the main kernel
   // of the previous step wrote last, which is still in L2 (67.5 -> 65.1 us on the
   // 128x128x256 column)
@@ -373,6 +388,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_density_c(Slots S, cons
     rp += b;
   }
   rhoN[(BATCH ? I.node_off : 0) + nidx(I.L, x, y, z)] = (rr - rp) / (rr + rp);
+  if (!BATCH && acc && t == 0) {   // slot 0 is a fluid slot: its thread gets here
+    acc[2 * slot] = 0.0;
+    acc[2 * slot + 1] = acc[2 * (slot ^ 1) + 1];
+  }
 }
 
 // a4 + a5 over the fluid slots
@@ -779,14 +798,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
   // step counter of the FP16 rounding: read from this step's slot, the next value
   // written to the other one (read by the next step's main kernel)
   const uint32_t step = rstep[slot];
-  if (blockIdx.x == 0) {
-    if (threadIdx.x == 0) rstep[slot ^ 1] = step + 1u;
-    if (BATCH) {
-      for (int k = threadIdx.x; k < n_inst; k += blockDim.x) acc[4 * k + 2 + (slot ^ 1)] = 0.0;
-    } else if (threadIdx.x == 0) {
-      acc[2 + (slot ^ 1)] = 0.0;
-    }
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rstep[slot ^ 1] = step + 1u;
   double dsum[1] = {0.0};
   if (pk != kNoNode) {
     const Inst &I = inst_of<BATCH>(S, single, k);
@@ -835,7 +847,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     if (dbg_delta) dbg_delta[noff + node] = delta;
     dsum[0] = (double)delta;
   }
-  // per instance: cumulative total acc[4k] and this step's slot acc[4k + 2 + slot]
+  // per instance: this step's sum and the cumulative sum, acc[4k + 2 slot] and acc[4k + 2 slot + 1]
   block_delta_inst<BATCH>(dsum[0], k, acc, slot);
 }
 

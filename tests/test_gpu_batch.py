@@ -48,7 +48,7 @@ def test_batch_matches_single_lattices():
             ref = L.get_state()
             ob = L.observables()
         assert np.abs(states[k] - ref).max() <= 1e-6, k
-        for key in ("mass_r", "mass_p", "mass_c", "consumed", "gas_saturation", "flux_in", "flux_out"):
+        for key in ("mass_r", "mass_p", "mass_c", "consumed", "rate", "gas_saturation", "flux_in", "flux_out"):
             assert abs(obs[k][key] - ob[key]) <= 1e-9 * max(1.0, abs(ob[key])), (k, key)
         assert obs[k]["step"] == 30 and obs[k]["n_fluid"] == ob["n_fluid"]
 

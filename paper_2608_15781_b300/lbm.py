@@ -196,9 +196,9 @@ def lbm_reaction(ctx):
     return r.value, c.value
 
 
-    """Enqueue one 16-byte copy of (rate, consumed) into host memory at address ``dst_ptr`` (two doubles,
-    """Enqueue copies of (rate, consumed) into host memory at address ``dst_ptr`` (two doubles,
-    page-locked), valid after the next synchronisation of the context's stream."""
+def lbm_reaction_async(ctx, dst_ptr):
+    """Enqueue one 16-byte copy of (rate, consumed) into host memory at address ``dst_ptr`` (two
+    doubles, page-locked), valid after the next synchronisation of the context's stream."""
     _check(load_library().lbm_reaction_async(ctx, dst_ptr), "lbm_reaction_async")
 
 

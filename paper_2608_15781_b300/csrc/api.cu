@@ -622,69 +622,74 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
   rc = rc ? rc : dalloc(b, (void **)&b.err, sizeof(int));
   rc = rc ? rc : dalloc(b, (void **)&b.rstep, 2 * sizeof(uint32_t));
   if (rc) return rc;
-  CK(cudaMemsetAsync(b.rhoN, 0, nodes * sizeof(float), b.stream));
-  CK(cudaMemsetAsync(b.nrm, 0, nodes * sizeof(float4), b.stream));
   CK(cudaMemsetAsync(b.err, 0, sizeof(int), b.stream));
   CK(cudaMemsetAsync(b.rstep, 0, 2 * sizeof(uint32_t), b.stream));
   {
-    // geometry kernels, one instance at a time (one-time set-up)
-    uint8_t *d_solid = nullptr, *d_react = nullptr;
-    float *d_theta = nullptr;
+    // geometry kernels, one instance at a time (one-time set-up).  The host mask,
+    // reactive flags and contact angles are staged in the normal field (16 B per node,
+    // unused until the first step; 6 B per node needed), copied on the context's stream
+    // so that each kernel reads its instance's data and the next copy follows it
+    auto up = [](long long x) { return (x + 255) / 256 * 256; };
     long long maxn = 0;
     for (int k = 0; k < n; ++k) maxn = std::max(maxn, b.h[k].d.L.n);
-    if (cudaMalloc((void **)&d_solid, maxn) != cudaSuccess || cudaMalloc((void **)&d_react, maxn) != cudaSuccess ||
-        cudaMalloc((void **)&d_theta, maxn * sizeof(float)) != cudaSuccess) {
-      (void)cudaGetLastError();
-      cudaFree(d_solid);
-      cudaFree(d_react);
-      cudaFree(d_theta);
-      return LBM_ENOMEM;
-    }
-    for (int k = 0; k < n && rc == LBM_OK; ++k) {
-      const Lattice &L = b.h[k].d.L;
-      if (cudaMemcpy(d_solid, geoms[k].solid, L.n, cudaMemcpyHostToDevice) != cudaSuccess ||
-          (geoms[k].reactive && cudaMemcpy(d_react, geoms[k].reactive, L.n, cudaMemcpyHostToDevice) != cudaSuccess)) {
-        rc = LBM_ECUDA;
-        break;
+    const size_t need = (size_t)(2 * up(maxn) + 4 * maxn);
+    struct Own {   // a buffer of its own when the normal field is too small (lattices of a few nodes)
+      void *p = nullptr;
+      ~Own() { cudaFree(p); }
+    } own;
+    uint8_t *d_solid = reinterpret_cast<uint8_t *>(b.nrm);
+    if (need > (size_t)nodes * sizeof(float4)) {
+      if (cudaMalloc(&own.p, need) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LBM_ENOMEM;
       }
+      d_solid = static_cast<uint8_t *>(own.p);
+    }
+    uint8_t *const d_react = d_solid + up(maxn);
+    float *const d_theta = reinterpret_cast<float *>(d_react + up(maxn));
+    for (int k = 0; k < n; ++k) {
+      const Lattice &L = b.h[k].d.L;
+      CK(cudaMemcpyAsync(d_solid, geoms[k].solid, L.n, cudaMemcpyHostToDevice, b.stream));
+      if (geoms[k].reactive) CK(cudaMemcpyAsync(d_react, geoms[k].reactive, L.n, cudaMemcpyHostToDevice, b.stream));
       k_geom<<<node_grid(L), node_block(), 0, b.stream>>>(L, d_solid, geoms[k].reactive ? d_react : nullptr,
                                                           theta_rad(params[k]), b.link + b.h[k].d.node_off,
                                                           b.nsv + b.h[k].d.node_off);
       if (geoms[k].theta_deg) {
-        if (cudaMemcpy(d_theta, geoms[k].theta_deg, L.n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
-          rc = LBM_ECUDA;
-          break;
-        }
+        CK(cudaMemcpyAsync(d_theta, geoms[k].theta_deg, L.n * sizeof(float), cudaMemcpyHostToDevice, b.stream));
         k_wall_theta<<<node_grid(L), node_block(), 0, b.stream>>>(L, b.link + b.h[k].d.node_off, d_theta,
                                                                   theta_rad(params[k]), b.nsv + b.h[k].d.node_off);
       }
-      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(b.stream) != cudaSuccess) rc = LBM_ECUDA;
+      CK(cudaGetLastError());
     }
-    cudaFree(d_solid);
-    cudaFree(d_react);
-    cudaFree(d_theta);
-    if (rc) return cuda_fail(b, cudaErrorUnknown);
+    if (own.p) CK(cudaStreamSynchronize(b.stream));   // before the buffer is freed
   }
   // slot space, built on the GPU (layout.cuh): per instance the block counts and
   // their scan, the totals to the host, then the fills at the instances' offsets
   std::vector<long long> nblk(n + 1, 0);
   for (int k = 0; k < n; ++k) nblk[k + 1] = nblk[k] + (b.h[k].d.L.n + kLayoutBlock - 1) / kLayoutBlock;
+  // the counts and totals are staged in the colour field (4 B per node, unused until
+  // the first step) when they fit, which they do unless the batch holds many lattices
+  // of a few nodes; else in a buffer of their own
   int *d_cnt = nullptr;
   long long *d_tot = nullptr;
-  if (cudaMalloc((void **)&d_cnt, 3 * (size_t)nblk[n] * sizeof(int)) != cudaSuccess ||
-      cudaMalloc((void **)&d_tot, 3 * (size_t)n * sizeof(long long)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    cudaFree(d_cnt);
-    return LBM_ENOMEM;
-  }
-  struct Scratch {   // frees the set-up buffers on every return path
-    int *c;
-    long long *t;
-    ~Scratch() {
-      cudaFree(c);
-      cudaFree(t);
+  struct Scratch {   // frees an own buffer on every return path
+    void *p = nullptr;
+    ~Scratch() { cudaFree(p); }
+  } scratch;
+  {
+    const size_t cnt_bytes = (3 * (size_t)nblk[n] * sizeof(int) + 255) / 256 * 256;
+    const size_t need = cnt_bytes + 3 * (size_t)n * sizeof(long long);
+    char *base = reinterpret_cast<char *>(b.rhoN);
+    if (need > (size_t)nodes * sizeof(float)) {
+      if (cudaMalloc(&scratch.p, need) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LBM_ENOMEM;
+      }
+      base = static_cast<char *>(scratch.p);
     }
-  } scratch{d_cnt, d_tot};
+    d_cnt = reinterpret_cast<int *>(base);
+    d_tot = reinterpret_cast<long long *>(base + cnt_bytes);
+  }
   int *const cf = d_cnt, *const cb = d_cnt + nblk[n], *const cw = d_cnt + 2 * nblk[n];
   for (int k = 0; k < n; ++k) {
     const Lattice &L = b.h[k].d.L;
@@ -768,6 +773,9 @@ int batch_create(Batch &b, int n, const lbm_geometry *geoms, const lbm_params *p
     CK(cudaMemcpyAsync(b.block_off, hblock.data(), hblock.size() * sizeof(int), cudaMemcpyHostToDevice, b.stream));
   CK(cudaStreamSynchronize(b.stream));
   if (bad) return LBM_EINVAL;
+  // the colour and normal fields held set-up data (geometry inputs, layout counts)
+  CK(cudaMemsetAsync(b.rhoN, 0, nodes * sizeof(float), b.stream));
+  CK(cudaMemsetAsync(b.nrm, 0, nodes * sizeof(float4), b.stream));
   CK(cudaMemsetAsync(b.buf0, 0, pop_bytes, b.stream));
   CK(cudaMemsetAsync(b.buf1, 0, pop_bytes, b.stream));
   b.fa = b.buf0;

@@ -67,6 +67,39 @@ def test_batch_step_matches_oracle_for_every_lattice():
         assert err < 5e-7, (k, err)
 
 
+def test_lattices_of_a_few_nodes():
+    """Lattices so small that lattice creation cannot stage its inputs (mask, layout
+    counts) in the colour and normal fields and takes buffers of its own: a 3x3x3
+    periodic box alone, and a batch of six 2x2x2 boxes and a 3x2x2 column.  One step
+    after 6 against the oracle; every lattice of the batch as it evolves alone."""
+    rng = np.random.default_rng(9)
+    shapes = [(2, 2, 2)] * 6 + [(3, 2, 2)]
+    bcs = [0] * 6 + [1]
+    solids = []
+    for s in shapes:
+        m = np.zeros(s, bool)
+        m.flat[rng.integers(0, m.size)] = True   # one solid node, the rest fluid
+        solids.append(m)
+    params = [lbm.Params(theta_deg=50.0 + 10 * k, k_rate=5e-3, sigma=0.02, u_in=0.004) for k in range(len(shapes))]
+    box = np.zeros((3, 3, 3), bool)
+    box[1, 1, 1] = True
+    cases = [([box], [lbm.Params(theta_deg=60.0, k_rate=5e-3, accel=(1e-5, 0, 0))], [0]), (solids, params, bcs)]
+    for sol, prm, bc in cases:
+        with lbm.Batch(sol, prm, bc_z=bc) as B:
+            B.step(6)
+            pre = [B.get_state(k) for k in range(len(sol))]
+            B.step(1)
+            post = [B.get_state(k) for k in range(len(sol))]
+        for k, (s, p, b) in enumerate(zip(sol, prm, bc)):
+            g = O.Geometry(solid=s, bc_z=b)
+            ref = O.step(O.State(f=pre[k].astype(np.float64)), g, _oparams(p, b)).f
+            err = np.abs(post[k].astype(np.float64) - ref)[:, g.fluid].max()
+            assert err < 5e-7, (k, err)
+            with lbm.Lattice(s, p, bc_z=b) as L:
+                L.step(7)
+                assert np.abs(L.get_state() - post[k]).max() <= 1e-6, k
+
+
 def test_tune_keeps_state_and_picks_candidates():
     solids, params, bcs = _cases()
     with lbm.Batch(solids, params, bc_z=bcs) as A, lbm.Batch(solids, params, bc_z=bcs) as B:

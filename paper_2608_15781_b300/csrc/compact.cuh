@@ -283,10 +283,11 @@ __device__ __forceinline__ void block_delta_inst(double d, int k, double *acc, i
 // Programmatic dependent launch of the step's kernels: let the next kernel of the
 // step be scheduled now (its blocks take the SM slots that this grid's last wave
 // frees), then wait until the kernel before this one has completed and its writes
-// are visible.  Called first thing by every step kernel, before any early return,
-// so a grid completes only after its predecessor did, and so on back to the first
-// kernel of the step.  Both instructions are no-ops for a launch without the
-// programmatic attribute.
+// are visible.  Every step kernel triggers first thing and has at least one thread
+// that waits (the thread of a fluid slot or of a list entry: the solid kernels are
+// not launched for an empty list), so a grid completes only after its predecessor
+// did, and so on back to the first kernel of the step.  Both instructions are no-ops
+// for a launch without the programmatic attribute.
 __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");

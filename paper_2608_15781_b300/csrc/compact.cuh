@@ -111,51 +111,57 @@ struct Store<float> {
     b = v.y;
   }
   static __device__ __forceinline__ void st2_r(float *__restrict__ f, unsigned ns, unsigned i, unsigned t, float a,
-                                               float b, uint32_t, uint32_t) {
+                                               float b, uint32_t) {
     reinterpret_cast<float2 *>(f)[i * ns + t] = make_float2(a, b);
   }
 };
 // FP32 -> FP16 with stochastic rounding: round away from zero with probability equal
 // to the discarded fraction of an FP16 spacing, so that per-step changes smaller than
 // half a spacing (which round-to-nearest drops every step) survive in expectation.
-// In the FP16 normal range the 13 discarded mantissa bits receive 13 random bits
-// before truncation; below it the rounding leans toward zero by less than one
-// spacing, so the stored deviations are scaled by 2^12 first (kHalfScale): the normal
-// range then starts at 1.5e-8 instead of 6.1e-5, and deviations up to 16 in
-// magnitude are representable (a larger one saturates; populations of a run near
-// rho = 1 stay far below).  The rounding is unbiased only if the random bits are
-// independent of the value's discarded bits, also from one step to the next: a node
-// whose value repeats must not round the same way every step.  The per-step stores
-// of the main kernel therefore draw their bits from the slot and a step counter
-// (node_seed); the one-time writes (start, set_state, ghost set-up) hash the value's
-// bits and the population's logical index p * ns + t (round_bits).  Both are
-// deterministic and reproducible.  Non-finite values get no random bits: added to a
-// NaN pattern such as 0x7fffffff they would carry into the sign bit and store a NaN
-// as -0.
+// The conversion is the hardware's (cvt.rs.f16x2.f32, sm_100 family): for each half,
+// the 13 discarded mantissa bits and 13 random bits are added and the sum truncated,
+// so the value rounds up exactly when they carry.  The low half takes its random bits
+// from rbits[12:0], the high half from rbits[28:16] (measured on the B300 with single
+// bits set against values whose discarded bits are known).  The stored deviations
+// are scaled by 2^12 first (kHalfScale): FP16's normal range then starts at 1.5e-8
+// instead of 6.1e-5, and deviations up to 16 in magnitude are representable
+// (populations of a run near rho = 1 stay far below).  The rounding is unbiased only
+// if the random bits are independent of the value's discarded bits, also from one
+// step to the next: a node whose value repeats must not round the same way every
+// step.  The per-step stores of the main kernel therefore draw their bits from the
+// slot and a step counter (node_seed); the one-time writes (start, set_state, ghost
+// set-up) hash the value's bits and the population's logical index p * ns + t
+// (round_bits).  Both are deterministic and reproducible.
+__device__ __forceinline__ uint32_t cvt_rs_half2(float hi, float lo, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+__device__ __forceinline__ __half half_rs(float x, uint32_t r13) {   // r13: 13 random bits
+  return __ushort_as_half((unsigned short)(cvt_rs_half2(0.f, x, r13) & 0xFFFFu));
+}
 __device__ __forceinline__ uint32_t round_bits(uint32_t bits, unsigned idx) {
   uint32_t h = (bits ^ idx) * 0x9E3779B9u;
   h ^= h >> 15;
   h *= 0x2C1B3C6Du;
   h ^= h >> 12;
-  return (bits & 0x7f800000u) == 0x7f800000u ? 0u : h;
+  return h;
 }
 constexpr float kHalfScale = 4096.f, kHalfUnscale = 1.f / 4096.f;
 __device__ __forceinline__ __half half_stochastic(float x, unsigned idx) {
-  const uint32_t bits = __float_as_uint(x);
-  return __float2half_rz(__uint_as_float(bits + (round_bits(bits, idx) >> 19)));
+  return half_rs(x, round_bits(__float_as_uint(x), idx) >> 19);
 }
 
 // The main kernel stores 45 values per node (and its outlet ghost's): it hashes
-// the slot t and the step counter once per node (node_seed) and gives population p
-// the top 13 bits of seed * K_p, K_p an odd constant per population -- one multiply
-// per store instead of a hash per store.  v is the node's post-collision rest
-// population, a function of every pulled value (through rho and C), so it is
-// non-finite whenever any stored value is: the seed is then 0 and no random bits
-// are added, which keeps a NaN a NaN (added to a NaN pattern such as 0x7fffffff
-// they would carry into the sign bit).  The value's bits do not enter the hash: a
-// seed drawn from them repeats whenever the node's state does, and a node at rest
-// then rounds the same way step after step (a steady mass drift: 36 mass units in
-// 5000 steps of a 64^3 droplet box, against 1.0 for FP32 storage).
+// the slot t and the step counter once per node (node_seed) and derives the random
+// word of a store from seed * K_p, K_p an odd constant per population -- one
+// multiply per store (per f^r_i / f^p_i pair) instead of a hash per store.  The
+// value's bits do not enter the hash: a seed drawn from them repeats whenever the
+// node's state does, and a node at rest then rounds the same way step after step (a
+// steady mass drift: 36 mass units in 5000 steps of a 64^3 droplet box, against 1.0
+// for FP32 storage).  v is the node's post-collision rest population, a function of
+// every pulled value (through rho and C); a node where it is not finite gets seed 0
+// (the conversion keeps a NaN a NaN whatever the random bits).
 __device__ __forceinline__ uint32_t node_seed(float v, unsigned t, uint32_t step) {
   uint32_t h = ((t * 0x85EBCA6Bu) ^ (step * 0xC2B2AE35u)) * 0x9E3779B9u;
   h ^= h >> 15;
@@ -165,14 +171,6 @@ __device__ __forceinline__ uint32_t node_seed(float v, unsigned t, uint32_t step
 }
 __device__ __forceinline__ uint32_t pop_random(uint32_t seed, int p) {
   return seed * ((0x9E3779B9u ^ ((uint32_t)p * 0x632BE5ABu)) | 1u);
-}
-
-// two FP32 values -> one 32-bit word of two FP16 halves, each rounded toward zero
-// (lo at the lower address)
-__device__ __forceinline__ uint32_t pack_half2_rz(float lo, float hi) {
-  uint32_t d;
-  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
 }
 
 template <>
@@ -187,12 +185,10 @@ struct Store<__half> {
   static __device__ __forceinline__ void st(__half *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v) {
     f[hidx(ns, p, t)] = half_stochastic(fmaf(v, kHalfScale, -kHalfScale * pop_ref(p)), p * ns + t);
   }
-  // the same rounding with the random word r supplied by the caller (top 13 bits
-  // used); the caller passes r = 0 for a node with a non-finite value (node_seed)
+  // the same rounding with the random word r supplied by the caller (its top 13 bits)
   static __device__ __forceinline__ void st_r(__half *__restrict__ f, unsigned ns, unsigned p, unsigned t, float v,
                                               uint32_t r) {
-    const float d = fmaf(v, kHalfScale, -kHalfScale * pop_ref(p));
-    f[hidx(ns, p, t)] = __float2half_rz(__uint_as_float(__float_as_uint(d) + (r >> 19)));
+    f[hidx(ns, p, t)] = half_rs(fmaf(v, kHalfScale, -kHalfScale * pop_ref(p)), r >> 19);
   }
   static __device__ __forceinline__ void ld2(const __half *__restrict__ f, unsigned ns, unsigned i, unsigned t,
                                              int iref, float &a, float &b) {
@@ -200,11 +196,12 @@ struct Store<__half> {
     a = fmaf(v.x, kHalfUnscale, WREF[iref]);
     b = fmaf(v.y, kHalfUnscale, 0.f);   // the reference of f^p is 0 (as in ld)
   }
+  // f^r_i (low half) and f^p_i (high half) of slot t with one random word r: f^p_i
+  // takes its top 13 bits (rbits[28:16] = r[31:19]), f^r_i bits 3 to 15
   static __device__ __forceinline__ void st2_r(__half *__restrict__ f, unsigned ns, unsigned i, unsigned t, float a,
-                                               float b, uint32_t ra, uint32_t rb) {
-    const float ua = __uint_as_float(__float_as_uint(fmaf(a, kHalfScale, -kHalfScale * WREF[i])) + (ra >> 19));
-    const float ub = __uint_as_float(__float_as_uint(b * kHalfScale) + (rb >> 19));
-    reinterpret_cast<uint32_t *>(f)[i * ns + t] = pack_half2_rz(ua, ub);
+                                               float b, uint32_t r) {
+    reinterpret_cast<uint32_t *>(f)[i * ns + t] =
+        cvt_rs_half2(b * kHalfScale, fmaf(a, kHalfScale, -kHalfScale * WREF[i]), r >> 3);
   }
 };
 
@@ -829,7 +826,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_main_c(Slots S, const _
     const uint32_t seed = node_seed(fr[Q - 1] + fp[Q - 1] + (I.P.reaction_mode == 0 ? g[Q7 - 1] : 0.f), t, step);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      Store<T>::st2_r(fout, ns, i, t, fr[i], fp[i], pop_random(seed, i), pop_random(seed, Q + i));
+      Store<T>::st2_r(fout, ns, i, t, fr[i], fp[i], pop_random(seed, i));
     }
     float g5;
     if (I.P.reaction_mode == 0) {

@@ -158,12 +158,12 @@ def test_precision_crop_against_fp64(storage):
     FP32 storage: conversion and gas saturation within 1e-5 at every 500 steps (measured
     8e-7 and 2.3e-6), the velocity at 4096 sampled fluid nodes within 2 % of the largest
     sampled speed (measured 1.4 %, at a node next to a moving interface; median 1e-6).
-    FP16 storage: within 3e-4 (measured up to 1.9e-4, 2.5e-4 with other rounding
+    FP16 storage: within 3e-4 (measured up to 1.8e-4, 2.5e-4 with other rounding
     seeds); the stochastic rounding is unbiased, and the error is the trajectory's
     response to the rounding noise (its sign and size change with the seed of the
     rounding bits).  The stated 1e-4 budget of the reduced-precision forms is met up
-    to step 2500, not at all later samples: see the next test for why no inexact run
-    can be held to it on this workload."""
+    to step 4000 (9.8e-5), not at the later samples: see the next test for why no
+    inexact run can be held to it on this workload."""
     obs, vel = _read_crop_reference()
     solid = synth.grf_mask((256, 256, 256), 12, 0.5, 3, periodic_z=True)[:64, :64, :64].copy()
     p = lbm.Params(tau=1.0, sigma=0.01, beta=0.7, theta_deg=60.0, k_rate=1e-3, diffusivity=0.05, c_init=1.0,
@@ -219,7 +219,7 @@ def test_precision_crop_conversion_is_set_by_fluctuations():
     FP64's by up to 1.3e-4 (measured 8e-6, 8.6e-5, 1.3e-4), against 8e-7 without it; the
     larger deviations have the sign of the FP16 runs' (lower conversion after step 2500),
     whose rounding noise acts as a fluctuation at every step.  So the FP16 error
-    (1.9e-4) is of the size of the trajectory's own sensitivity, and the check is that it
+    (1.8e-4) is of the size of the trajectory's own sensitivity, and the check is that it
     stays within 3x of the largest FP32 deviation from a perturbed start."""
     fp32 = [_crop_conversion_errors(0, d) for d in range(3)]
     fp16 = _crop_conversion_errors(1)

@@ -158,8 +158,8 @@ def test_precision_crop_against_fp64(storage):
     FP32 storage: conversion and gas saturation within 1e-5 at every 500 steps (measured
     8e-7 and 2.3e-6), the velocity at 4096 sampled fluid nodes within 2 % of the largest
     sampled speed (measured 1.4 %, at a node next to a moving interface; median 1e-6).
-    FP16 storage: within 3e-4 (measured up to 1.8e-4, 2.5e-4 with other rounding
-    seeds); the stochastic rounding is unbiased, and the error is the trajectory's
+    FP16 storage: within 3e-4 (measured up to 1.8e-4; 1.3e-4 to 2.9e-4 with four other
+    seeds of the rounding bits); the stochastic rounding is unbiased, and the error is the trajectory's
     response to the rounding noise (its sign and size change with the seed of the
     rounding bits).  The stated 1e-4 budget of the reduced-precision forms is met up
     to step 4000 (9.8e-5), not at the later samples: see the next test for why no

@@ -190,7 +190,9 @@ def test_directional_derivatives_against_fp64_central_differences():
     crossed inside +-h), and against the FP64 adjoint linearised along the GPU's own FP32
     trajectory (reported).
 
-    Bounds: median 5e-4, every direction 2e-3, u_in 1e-5.  The directional derivatives
+    Bounds: the 16 derivatives as one vector within 1e-3 in the relative 2-norm
+    (measured 2.0e-4), median 5e-4, every direction 2e-3 (15 of 16 within 1e-3, the
+    worst 1.08e-3), u_in 1e-5.  The directional derivatives
     of this discrete map are sensitive to rounding-level changes of the state: a random
     1e-7 perturbation of the start moves the FP64 central differences themselves by
     2e-4 - 5e-3 per direction (interfaces whose normal n = grad / |grad| rounds
@@ -227,11 +229,12 @@ def test_directional_derivatives_against_fp64_central_differences():
         d1, d2 = central(fun, h), central(fun, h / 2)
         return (4 * d2 - d1) / 3, abs(d1 - d2)
 
-    rel, rel_own, rel_traj, spread = [], [], [], []
+    rel, rel_own, rel_traj, spread, pairs = [], [], [], [], []
     for _ in range(16):
         v = rng.standard_normal(shape) * solid
         fd, sp = richardson(lambda e: A.conversion_forward(g, op, f0, th64 + e * v, nsteps), 1e-2)
         gpu, along = float((dth * v).sum()), float((dth_along * v).sum())
+        pairs.append((gpu, fd))
         rel.append(abs(gpu - fd) / abs(fd))
         rel_own.append(abs(gpu - along) / abs(along))
         rel_traj.append(abs(along - fd) / abs(fd))
@@ -243,7 +246,13 @@ def test_directional_derivatives_against_fp64_central_differences():
     print("\nGPU adjoint vs FP64 differences:", fmt(rel), "\nGPU adjoint vs FP64 adjoint along the GPU trajectory:",
           fmt(rel_own), "\nFP64 adjoint along the GPU trajectory vs FP64 differences:", fmt(rel_traj),
           "\n|D(h) - D(h/2)|:", fmt(spread), "\nu_in:", abs(du - fdu) / abs(fdu), abs(du - du_along) / abs(du_along))
+    # the 16 directional derivatives as one vector (the gradient's projection on the
+    # random directions): its relative error in the 2-norm
+    gv, fv = np.array(pairs).T
+    agg = np.linalg.norm(gv - fv) / np.linalg.norm(fv)
+    print("projected gradient, relative 2-norm error:", agg)
     assert spread.max() < 1e-3, spread
+    assert agg < 1e-3, agg
     assert np.median(rel) < 5e-4 and rel.max() < 2e-3, rel
     assert abs(du - fdu) < 1e-5 * abs(fdu), (du, fdu)
 

@@ -391,8 +391,10 @@ def run_native(args):
     # destroy.  Measured before the clock-sampled timed region: a run of nvidia-smi from
     # this process slows its later CUDA API calls (lattice creation +1.5 ms, destroy
     # +3.8 ms on the 128x128x256 column, measured), which a user's run does not pay.  An
-    # untimed create / step / destroy first loads the kernels (the process's first
-    # creation also pays the lazy loading of the library's modules, about 2 ms).
+    # untimed lattice, created and stepped first and destroyed after the timed leg, loads
+    # the kernels (the process's first creation pays the lazy loading of the library's
+    # modules, about 1 ms; a creation right after a destroy pays about as much for the
+    # memory the destroy released).
     e2e = None
     if not args.no_e2e:
         # the host mask in page-locked memory, as the step results are
@@ -405,7 +407,6 @@ def run_native(args):
         Lw.step(2)
         Lw.reaction_async(base)
         Lw.observables()
-        Lw.close()
         barrier()
         t0 = time.perf_counter()
         L2 = lbm.Lattice(solid_h, head, bc_z=wl.bc_z, stream=stream.cuda_stream)
@@ -417,6 +418,7 @@ def run_native(args):
         L2.close()
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        Lw.close()
         rates = ring.numpy().reshape(-1, 2)
         assert abs(rates[-1, 1] - ob2["consumed"]) <= 1e-9 * max(1.0, abs(ob2["consumed"]))
         h2d = N * 1                                  # the mask
